@@ -1,0 +1,174 @@
+"""Physics pins of the oracle on whole flows (no GPU):
+
+- body-force Poiseuille channel (Sec. 5.1): parabolic profile, second-order
+  convergence of the global relative error the paper defines;
+- viscous decay of shear waves and Taylor-Green vortices at the rate
+  nu |k|^2 (Eq. 30-32), the same for every orientation at a != 1, with a
+  negative control that switches the isotropy correction (Eq. 23-24) off;
+- Galilean invariance of the decay rate under a uniform boost, with a
+  negative control that switches the GI correction (Eq. 25-26) off;
+- transient Couette flow against its Fourier series (Sec. 5.2), which pins
+  the moving-wall bounce-back of Eq. 57-59;
+- global mass conservation to rounding.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2103_02119_gb300 import workloads as W
+
+
+def make(orc, wl, **kw):
+    p = orc.OracleParams.make(wl.nx, wl.ny, wl.a, wl.cs2, wl.omega, Fx=wl.Fx,
+                              Fy=wl.Fy, periodic_x=wl.periodic_x,
+                              periodic_y=wl.periodic_y, wall_u=wl.wall_u,
+                              use_iso_corr=kw.pop("iso", wl.use_iso_corr),
+                              use_gi_corr=kw.pop("gi", wl.use_gi_corr), **kw)
+    o = orc.Oracle(p, wl.mask)
+    o.init_fields(wl.rho, wl.ux, wl.uy)
+    return o
+
+
+def poiseuille_error(orc, ny, steps, scheme="rc"):
+    wl = W.poiseuille(ny=ny)
+    o = make(orc, wl, scheme=scheme)
+    o.step(steps)
+    rho, ux, uy = o.moments()
+    H, U = wl.info["H"], wl.info["U"]
+    y = (np.arange(ny) + 0.5) * wl.a
+    ua = (U * (1 - (y - H / 2) ** 2 / (H / 2) ** 2))[:, None] * np.ones((1, wl.nx))
+    # Sec. 5.1: sum ||u_c - u_a|| / sum ||u_a|| over the domain
+    err = np.sqrt((ux - ua) ** 2 + uy ** 2).sum() / np.abs(ua).sum()
+    return err, rho, uy
+
+
+@pytest.mark.parametrize("scheme", ["rc", "rnr"])
+def test_poiseuille_config1(orc, scheme):
+    """32 x 32, a = 0.5, nu = 0.1, u_max = 0.01, 5000 steps from rest."""
+    err, rho, uy = poiseuille_error(orc, 32, 5000, scheme)
+    assert err < 3e-3
+    assert np.abs(uy).max() < 1e-14
+    assert abs(math.fsum(rho.ravel()) / rho.size - 1.0) < 1e-13
+
+
+def test_poiseuille_second_order(orc):
+    e16, _, _ = poiseuille_error(orc, 16, 3000)
+    e32, _, _ = poiseuille_error(orc, 32, 5000)
+    assert 3.5 < e16 / e32 < 4.5
+
+
+def decay_rate(orc, wl, steps, every, **kw):
+    """Fit of log amplitude of the initial velocity pattern (advected with
+    the background velocity) against time; returned relative to nu |k|^2 of
+    the pattern (TGV: 2 nu k^2)."""
+    o = make(orc, wl, **kw)
+    info = wl.info
+    bg = info.get("background", (0.0, 0.0))
+    ux0, uy0 = wl.ux - bg[0], wl.uy - bg[1]
+    x, y = W.coords(wl.nx, wl.ny, wl.a)
+    k = info["k"]
+    ts, amps = [], []
+    for n in range(0, steps + 1, every):
+        if n:
+            o.step(every)
+        _, u, v = o.moments()
+        if bg != (0.0, 0.0):
+            p1, p2 = info["phases"]
+            xs, ys = x - bg[0] * n, y - bg[1] * n
+            px = np.sin(k * xs + p1) * np.cos(k * ys + p2)
+            py = -np.cos(k * xs + p1) * np.sin(k * ys + p2)
+        else:
+            px, py = ux0, uy0
+        amps.append(((u - bg[0]) * px + (v - bg[1]) * py).sum() / (px * px + py * py).sum())
+        ts.append(n)
+    slope = np.polyfit(ts[1:], np.log(np.abs(amps[1:])), 1)[0]
+    mult = 2.0 if (wl.name.startswith("tgv") or info.get("direction") == "diag") else 1.0
+    return -slope / (mult * info["nu"] * k * k)
+
+
+@pytest.mark.parametrize("a", [0.5, 0.25])
+@pytest.mark.parametrize("direction", ["x", "y"])
+def test_axis_shear_waves_decay_at_nu_k2(orc, a, direction):
+    cs2 = W.stable_cs2(a)
+    wl = W.shear_wave(32, int(round(32 / a)), a, cs2, 0.01, direction, u0=0.01, seed=3)
+    r = decay_rate(orc, wl, 1000, 100)
+    assert abs(r - 1) < 0.01
+
+
+@pytest.mark.parametrize("a", [0.5, 0.25])
+@pytest.mark.parametrize("kind", ["tgv", "diag"])
+def test_isotropic_decay_and_negative_control(orc, a, kind):
+    """Flows with normal strain (d_x u_x != 0) decay at nu |k|^2 only when the
+    isotropy correction is on."""
+    cs2 = W.stable_cs2(a)
+    ny = int(round(32 / a))
+    if kind == "tgv":
+        wl = W.taylor_green(32, ny, a, cs2, 0.01, u0=0.01, seed=2)
+    else:
+        wl = W.shear_wave(32, ny, a, cs2, 0.01, "diag", u0=0.01, seed=2)
+    assert abs(decay_rate(orc, wl, 1000, 100) - 1) < 0.02
+    assert abs(decay_rate(orc, wl, 1000, 100, iso=0) - 1) > 0.2
+
+
+@pytest.mark.parametrize("a,boost,gi_off_min", [(0.5, (0.05, 0.0), 0.01),
+                                                (0.25, (0.0, 0.05), 0.05)])
+def test_decay_rate_galilean_invariant(orc, a, boost, gi_off_min):
+    cs2 = W.stable_cs2(a)
+    ny = int(round(32 / a))
+    rest = W.taylor_green(32, ny, a, cs2, 0.01, u0=0.005, seed=4)
+    moving = W.taylor_green(32, ny, a, cs2, 0.01, u0=0.005, seed=4, background=boost)
+    r0 = decay_rate(orc, rest, 2000, 200)
+    r1 = decay_rate(orc, moving, 2000, 200)
+    r1_off = decay_rate(orc, moving, 2000, 200, gi=0)
+    assert abs(r1 / r0 - 1) < 0.008
+    assert abs(r1_off / r0 - 1) > gi_off_min
+
+
+@pytest.mark.parametrize("a,cs2,ny", [(0.25, 0.04, 40), (0.1, 0.005, 100)])
+def test_transient_couette_series(orc, a, cs2, ny):
+    wl = W.couette(ny=ny, a=a, cs2=cs2, tau=0.8, U=0.02)
+    o = make(orc, wl)
+    nu, U, H = wl.info["nu"], wl.info["U"], wl.info["H"]
+    y = (np.arange(ny) + 0.5) * a
+    n_terms = np.arange(1, 201)[:, None]
+    t = 0
+    for T in (0.02, 0.05, 0.1, 0.2):
+        n = int(round(T * H * H / nu))
+        o.step(n - t)
+        t = n
+        _, u, v = o.moments()
+        series = U * y / H - (2 * U / np.pi) * (
+            np.exp(-n_terms ** 2 * np.pi ** 2 * nu * t / H ** 2) / n_terms
+            * np.sin(n_terms * np.pi * (1 - y / H))).sum(0)
+        assert np.abs(u.mean(axis=1) - series).max() < 1e-3 * U
+        assert np.abs(u - u.mean(axis=1, keepdims=True)).max() < 1e-15
+
+
+def test_global_mass_conserved_to_rounding(orc):
+    wl = W.taylor_green(24, 48, 0.5, W.stable_cs2(0.5), 0.02, u0=0.02, seed=5)
+    wl = wl.with_(mask=W.random_obstacles(24, 48, seed=1, coverage=0.08),
+                  periodic_y=0, wall_u=((0, 0), (0, 0), (0, 0), (0.01, 0)))
+    o = make(orc, wl)
+    m0 = math.fsum(o.get_f().ravel())
+    o.step(300)
+    m1 = math.fsum(o.get_f().ravel())
+    # each of 300 steps may move the total by a few ulp per cell
+    assert abs(m1 - m0) <= 300 * wl.cells * 4 * 2.2e-16
+
+
+def test_solid_rows_equal_implicit_walls(orc):
+    """A channel closed by rows of solid nodes (periodic y) is the same
+    lattice as one closed by the implicit half-way walls."""
+    wl = W.poiseuille(ny=16, nx=8)
+    o = make(orc, wl)
+    o.step(400)
+    walled = o.moments()
+    mask = np.zeros((18, 8), np.uint8)
+    mask[0] = mask[17] = 1
+    wl2 = wl.with_(ny=18, periodic_y=1, mask=mask)
+    o2 = make(orc, wl2)
+    o2.step(400)
+    masked = [m[1:17] for m in o2.moments()]
+    for w_, m_ in zip(walled, masked):
+        np.testing.assert_allclose(m_, w_, rtol=0, atol=1e-15)
