@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused RC-LBM collide-and-stream step on GB300.
+
+Workload (default): lid-driven square cavity on a rectangular lattice,
+2048 x 8192 cells at a = dy/dx = 0.25 (physical aspect 1), c_s^2 = 0.04,
+lid speed 0.05, Re = 1000, FP32 deviation storage, started from rest.  One
+benchmark step is one lattice time step over the whole grid (one launch of
+the step kernel).  Metric: MLUPS (million lattice-cell updates per second),
+whole job, with the state resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+prints one JSON line.  With --impl reference the FP64 CPU oracle is timed
+instead, on a bounded sample of the same workload.  Under torchrun (N > 1)
+each rank runs an independent replica (the solver does not shard across
+GPUs); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {32: 72, 64: 144}   # 9 loads + 9 stores of the storage type
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=2048)
+    ap.add_argument("--ny", type=int, default=8192)
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--e2e-chunk", type=int, default=100,
+                    help="lattice steps per end-to-end call sequence")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--block-x", type=int, default=0)
+    ap.add_argument("--bands", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2103_02119_gb300 import workloads as W
+    return W.cavity(args.nx, args.ny, 0.25, 0.04, 0.05, 1000.0)
+
+
+def workload_config(args, wl):
+    return {
+        "workload": f"lid-driven cavity {wl.nx}x{wl.ny} cells, a=0.25, Re=1000, "
+                    f"lid u=0.05, FP{args.precision} storage",
+        "nx": wl.nx, "ny": wl.ny, "cells": wl.cells, "a": wl.a, "cs2": wl.cs2,
+        "lid_u": 0.05, "Re": 1000, "nu": wl.info["nu"],
+        "layout": "SoA 9 planes, two buffers, pull streaming",
+        "l2": "inputs larger than L2 (state of %d MB per buffer vs 129 MB L2), no flush"
+              % (9 * wl.cells * (args.precision // 8) // 2 ** 20),
+        "parallelism": "replicas" if args.gpus > 1 else "single GPU",
+    }
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------- roofline --
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def step_kernel_hash():
+    h = hashlib.sha256()
+    for f in ("rc_step.cu", "lbm_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2103_02119_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(precision, cells):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this
+    grid, or None when the kernel has changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "rc_step_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get(f"fp{precision}")
+    if not e or e.get("kernel_sha") != step_kernel_hash():
+        return None
+    return e["dram_bytes_per_cell"] * cells
+
+
+# ------------------------------------------------------------- GPU timing --
+
+def time_steps(lat, torch, steps, warmup, barrier):
+    stream = torch.cuda.current_stream()
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = lat.launch_count
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1) / 1e3, lat.launch_count - l0
+
+
+def e2e(lat, wl, torch, chunk, reps):
+    """Through the public API with host buffers: upload the initial fields
+    from pinned host memory, advance `chunk` steps, read the fields back."""
+    import numpy as np
+    N = wl.cells
+    pin = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(6)]
+    host = [t.numpy() for t in pin]
+    host[0][:] = 1.0
+    host[1][:] = 0.0
+    host[2][:] = 0.0
+    lat.init_fields(host[0], host[1], host[2])
+    lat.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    from paper_2103_02119_gb300 import lbm
+    for _ in range(reps):
+        lat.init_fields(host[0], host[1], host[2])
+        lat.step(chunk)
+        lbm.lbm_moments(lat.h, N, host[3], host[4], host[5])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    assert np.isfinite(host[3]).all()
+    return {"value": N * chunk * reps / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": 3 * N * 8,
+            "chunk_lattice_steps": chunk,
+            "note": "one e2e step = lbm_init_fields from pinned host rho/u, "
+                    f"lbm_step({chunk}), lbm_moments to pinned host rho/u"}
+
+
+# -------------------------------------------------------------- oracle arm --
+
+def oracle_mlups(wl, rows, seconds, warmup_steps=0, steps=None):
+    """The FP64 oracle as it stands, all host cores, on the same cavity with
+    `rows` rows; returns (MLUPS, threads, steps, sample description)."""
+    import oracle
+    sub = wl.with_(ny=rows)
+    p = oracle.OracleParams.make(sub.nx, sub.ny, sub.a, sub.cs2, sub.omega,
+                                 periodic_x=sub.periodic_x, periodic_y=sub.periodic_y,
+                                 wall_u=sub.wall_u)
+    o = oracle.Oracle(p)
+    if warmup_steps:
+        o.step(warmup_steps)
+    if steps is None:
+        t = time.perf_counter()
+        o.step(1)
+        one = time.perf_counter() - t
+        steps = max(1, min(50, int(seconds / max(one, 1e-6))))
+    t = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t
+    desc = f"{sub.nx}x{rows} cells of the same cavity parameters, {steps} FP64 oracle steps"
+    return sub.cells * steps / dt / 1e6, o.threads, steps, desc, dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    wl = workload(args)
+    # each benchmark step is one oracle step on a 2048 x 64 slab of the cavity
+    rows = 64
+    mlups, threads, steps, desc, dt = oracle_mlups(
+        wl, rows, 0, warmup_steps=args.warmup, steps=max(1, args.steps))
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / max(1, args.steps) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, wl),
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- main --
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2103_02119_gb300.lbm import Lattice
+    wl = workload(args)
+    stream = torch.cuda.current_stream()
+    lat = Lattice.from_workload(wl, precision=args.precision, stream=stream,
+                                block_x=args.block_x, bands=args.bands)
+    with ClockSampler(local) as clk:
+        secs, launches = time_steps(lat, torch, args.steps, args.warmup, barrier)
+    if dist is not None:
+        t = torch.tensor([secs], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    cells = wl.cells
+    value = world * cells * args.steps / secs / 1e6
+    per_launch = secs / args.steps
+    algo_bytes = BYTES_PER_CELL[args.precision] * cells
+    peak, peak_kind = measured_peaks()
+    achieved = algo_bytes / per_launch / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profiled_traffic(args.precision, cells),
+                "peak_kind": peak_kind, "kernel": f"rc_step_kernel<fp{args.precision}>",
+                "algorithmic_bytes_per_cell": BYTES_PER_CELL[args.precision]}
+    e2e_res = e2e(lat, wl, torch, args.e2e_chunk, args.e2e_steps)
+
+    fp64 = None
+    if not args.no_fp64 and args.precision == 32:
+        lat.close()
+        lat64 = Lattice.from_workload(wl, precision=64, stream=stream)
+        s64, _ = time_steps(lat64, torch, max(20, args.steps // 20), 5, barrier)
+        n64 = max(20, args.steps // 20)
+        a64 = BYTES_PER_CELL[64] * cells / (s64 / n64) / 1e9
+        fp64 = {"value": cells * n64 / s64 / 1e6, "unit": "MLUPS", "steps": n64,
+                "roofline": {"bound": "alu", "hbm_achieved": a64, "hbm_peak": peak,
+                             "unit": "GB/s", "hbm_frac": a64 / peak}}
+        lat64.close()
+    else:
+        lat.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        mlups, threads, steps, desc, _ = oracle_mlups(wl, wl.ny, args.cpu_seconds)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_launch * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": f"f{args.precision}", "data": "synthetic",
+            "config": workload_config(args, wl), "roofline": roofline,
+            "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches,
+            "clocks": clk.summary(), "fp64": fp64,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * lbm.h -- C ABI of the GB300-native rectangular central-moment lattice
+ * Boltzmann library (liblbm_gb300.so).
+ *
+ * The library advances the D2Q9 RC-LBM of Yahia & Premnath, "Central Moment
+ * Lattice Boltzmann Method on a Rectangular Lattice" (arXiv 2103.02119),
+ * Sec. 4: per cell and time step it maps the nine distributions to raw and
+ * central moments (Eq. 4, App. B), relaxes the central moments towards the
+ * Maxwell-matched equilibria carrying the isotropy and Galilean-invariance
+ * corrections (Eq. 23-27, 37-40, 49), maps back (Eq. 55, App. A) and streams
+ * along the rectangular links e_i = (+-1, +-a) (Eq. 2), with half-way
+ * bounce-back walls (Sec. 5.1, Eq. 57-59) and body forcing in the same pass.
+ * Every step runs as hand-written CUDA kernels for sm_103a on one GPU; there
+ * is no CPU fallback.
+ *
+ * Lattice units: dx = dt = 1, dy = a.  Cell (x, y), 0 <= x < nx, 0 <= y < ny,
+ * has linear index y*nx + x (x fastest).  Direction order 0..8 is the order
+ * of Eq. 2: (0,0) (1,0) (0,a) (-1,0) (0,-a) (1,a) (-1,a) (-1,-a) (1,-a).
+ *
+ * Conventions of every entry point:
+ *   - The return value is an lbm_status; nothing is thrown across the ABI.
+ *   - Host arrays are owned by the caller and copied; the library keeps no
+ *     pointer to them after the call returns.  Device arrays (on_device != 0)
+ *     must be device memory of the handle's device, owned by the caller.
+ *   - Work is issued on the CUDA stream given to lbm_create (borrowed, never
+ *     destroyed; NULL = the legacy default stream).  lbm_step and the
+ *     on_device variants are asynchronous on that stream; calls that read
+ *     into host memory synchronise it before returning.
+ *   - On an error the handle stays valid and lbm_last_error describes the
+ *     failure.  Invalid parameters are rejected on the host before any
+ *     device work.
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_handle lbm_handle;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID = -1,  /* argument or parameter rejected; nothing was done */
+    LBM_ERR_OOM = -2,      /* a device or host allocation failed              */
+    LBM_ERR_CUDA = -3,     /* a CUDA call failed (see lbm_last_error)          */
+    LBM_ERR_UNSTABLE = -4, /* lbm_diagnostics found non-finite fluid cells     */
+    LBM_ERR_STATE = -6     /* state buffer of the wrong size                   */
+} lbm_status;
+
+/* Number of doubles written by lbm_diagnostics. */
+#define LBM_DIAG_COUNT 7
+
+typedef struct {
+    int32_t nx, ny;        /* cells along x and y, each >= 3                    */
+    double a;              /* grid aspect ratio dy/dx (Sec. 2.1), > 0           */
+    double cs2;            /* speed of sound squared, 0 < cs2 < min(1, a^2)     */
+    double omega[9];       /* relaxation rates of Eq. 5 (Lambda), each in
+                              [0, 2], omega[3] and omega[4] > 0.  Shear
+                              viscosity nu = cs2 (1/omega[4] - 1/2) (Eq. 32),
+                              omega[5] should equal omega[4]; bulk viscosity
+                              from omega[3] (Eq. 33).  omega[0..2] have no
+                              effect (conserved moments).                      */
+    double Fx, Fy;         /* uniform body-force density (Sec. 4, Phi^c)        */
+    double rho0;           /* reference density of the stored deviations
+                              f_i - w_i rho0 (w_i: rest equilibrium weights);
+                              0 stores raw f_i                                  */
+    int32_t precision;     /* 32: FP32 storage and arithmetic, 64: FP64         */
+    int32_t periodic_x;    /* 1: periodic along x; 0: walls at x = -1, x = nx   */
+    int32_t periodic_y;    /* 1: periodic along y; 0: walls at y = -1, y = ny   */
+    double wall_u[4][2];   /* wall velocity (Ux, Uy) of the left, right,
+                              bottom and top walls; a node outside the domain
+                              in both x and y (a corner) belongs to the bottom
+                              or top wall                                        */
+    int32_t use_iso_corr;  /* 1: isotropy correction m^{eq,s} (Eq. 23-24)       */
+    int32_t use_gi_corr;   /* 1: Galilean-invariance correction (Eq. 25-26)     */
+    int32_t block_x;       /* step kernel tuning: threads per block along x,
+                              0 = automatic, else one of 32, 64, 128, 256        */
+    int32_t bands;         /* step kernel tuning: number of row bands,
+                              0 = automatic                                     */
+    int32_t scheme;        /* 0: RC-LBM collision (Sec. 4); -1: no collision
+                              (streaming and bounce-back only, a test mode in
+                              which a step is a permutation of the state)       */
+} lbm_params;
+
+/* Fill *p with defaults: 64 x 64 periodic, a = 1, cs2 = 1/3, all omega 1,
+ * no force, rho0 = 1, precision 32, both corrections on, automatic tuning,
+ * RC-LBM scheme. */
+lbm_status lbm_params_init(lbm_params* p);
+
+/* Create a lattice.  p: parameters (copied).  solid_mask: nullable, nx*ny
+ * bytes in cell order, non-zero = stationary solid node (copied); a fluid
+ * cell whose 8 neighbours are all wall or solid nodes is made solid.
+ * cuda_stream: a cudaStream_t or NULL (borrowed).  The new handle owns all of
+ * its device memory; its state is the rest state rho = 1, u = 0.
+ * Errors: LBM_ERR_INVALID (bad parameters, NULL out), LBM_ERR_OOM,
+ * LBM_ERR_CUDA.  *out is NULL on failure. */
+lbm_status lbm_create(const lbm_params* p, const uint8_t* solid_mask,
+                      void* cuda_stream, lbm_handle** out);
+
+/* Destroy a handle and free its device memory.  NULL is ignored. */
+void lbm_destroy(lbm_handle* h);
+
+/* Set the state to the equilibrium f_i = f_i^eq(rho, u) of Sec. 4
+ * (T^-1 F(-u) applied to the Maxwell-matched central moments) at every fluid
+ * cell.  rho, ux, uy: nx*ny doubles each, nullable (rho = 1, u = 0); host
+ * memory, or device memory when on_device != 0.  Resets the step counter and
+ * the residual reference of lbm_diagnostics. */
+lbm_status lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
+                           const double* uy, int on_device);
+
+/* Advance nsteps >= 0 time steps (collide + stream, Sec. 4).  Asynchronous:
+ * the return value reports launch errors only. */
+lbm_status lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Replace the uniform body force (takes effect from the next step). */
+lbm_status lbm_set_force(lbm_handle* h, double Fx, double Fy);
+
+/* Macroscopic fields of the current state: rho = sum_i f_i and
+ * u = (sum_i f_i e_i + F/2) / rho (Sec. 4, last step).  Each output is
+ * nx*ny doubles, nullable; solid cells give 0.  Host outputs synchronise the
+ * stream; device outputs (on_device != 0) are written asynchronously. */
+lbm_status lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy,
+                       int on_device);
+
+/* Distributions f_i(x, t) of the current state (after streaming), as
+ * doubles, 9*nx*ny in plane-major order f[i*nx*ny + y*nx + x]; solid cells
+ * give 0.  Host or device memory as above. */
+lbm_status lbm_get_f(lbm_handle* h, double* f, int on_device);
+
+/* Set the current state from distributions in the layout of lbm_get_f
+ * (rounded to the handle's precision).  Values at solid cells are ignored.
+ * Resets the step counter and the residual reference. */
+lbm_status lbm_set_f(lbm_handle* h, const double* f, int on_device);
+
+/* FP64 global diagnostics over the fluid cells, synchronous:
+ *   out[0] mass  = sum rho; the stored values are summed exactly (fixed
+ *                  point), so a permutation of the state gives the same bits
+ *   out[1] sum rho u_x, out[2] sum rho u_y, out[3] sum rho |u|^2 / 2
+ *   out[4] steady residual sqrt(sum |u(n) - u(m)|^2) / ((n - m) sqrt(sum
+ *          |u(n)|^2)) against the state m of the previous call, or -1 when
+ *          there is no previous call (or n == m)
+ *   out[5] number of fluid cells with a non-finite rho or u
+ *   out[6] step counter n
+ * Returns LBM_ERR_UNSTABLE (with out filled) when out[5] > 0. */
+lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]);
+
+/* Size in bytes of the raw state (checkpoint) of a handle. */
+size_t lbm_state_bytes(const lbm_handle* h);
+
+/* Copy the raw device state (storage precision, internal layout) to / from
+ * host memory of exactly lbm_state_bytes bytes, synchronously.  A state
+ * copied out and back continues bit-identically.  LBM_ERR_STATE on a size
+ * mismatch. */
+lbm_status lbm_get_state(lbm_handle* h, void* host, size_t bytes);
+lbm_status lbm_set_state(lbm_handle* h, const void* host, size_t bytes);
+
+/* Time steps taken since the last init / set call. */
+int64_t lbm_step_count(const lbm_handle* h);
+
+/* Number of kernel launches issued by lbm_step so far on this handle. */
+int64_t lbm_launch_count(const lbm_handle* h);
+
+/* Message of the last error on h (or of the last failed lbm_create when h is
+ * NULL); never NULL.  Not thread-safe. */
+const char* lbm_last_error(const lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

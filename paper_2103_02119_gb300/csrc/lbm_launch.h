@@ -1,0 +1,46 @@
+// lbm_launch.h -- host-side entry points of the kernels (internal to the
+// library; the public interface is include/lbm.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Fixed-point accumulator of the exact mass: value = sum_k limb[k] 2^(24k - 144).
+constexpr int kMassLimbs = 8;
+constexpr int kMassShift = 144;
+// Per-block partial results of the diagnostics reduction.
+struct DiagPartial {
+    double mx, my, en, dres, ures;  // sum rho ux, rho uy, rho|u|^2/2, |du|^2, |u|^2
+    long long nonfinite;
+    long long limb[kMassLimbs];
+};
+
+template <typename T>
+cudaError_t launch_step(const T* fin, T* fout, const KParams<T>& p, int bx, int nbands,
+                        cudaStream_t s);
+template <typename T>
+int step_occupancy(int bx, bool mask);
+
+// f = f^eq(rho, u) (device inputs, nullable), written in pull-scheme form.
+template <typename T>
+cudaError_t launch_init(T* f, const AuxParams& p, const double* rho, const double* ux,
+                        const double* uy, cudaStream_t s);
+// state from post-stream distributions (device, 9 planes of nx*ny doubles)
+template <typename T>
+cudaError_t launch_set_f(T* f, const AuxParams& p, const double* fin, cudaStream_t s);
+// post-stream distributions / moments of the state (device outputs)
+template <typename T>
+cudaError_t launch_get_f(const T* f, const AuxParams& p, double* fout, cudaStream_t s);
+template <typename T>
+cudaError_t launch_moments(const T* f, const AuxParams& p, double* rho, double* ux,
+                           double* uy, cudaStream_t s);
+// diagnostics: per-block partials into `part` (nblocks entries) then a final
+// reduction into part[nblocks]; uprev (2*nx*ny doubles) is read (if
+// have_prev) and overwritten with the current velocity.
+template <typename T>
+cudaError_t launch_diag(const T* f, const AuxParams& p, double* uprev, int have_prev,
+                        DiagPartial* part, int nblocks, cudaStream_t s);
+
+}  // namespace lbm

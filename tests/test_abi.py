@@ -1,0 +1,109 @@
+"""The C ABI without a GPU: the library loads, exports every entry point that
+include/lbm.h declares, the ctypes mirror of lbm_params has the C layout, and
+invalid parameters are rejected on the host before any device work."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2103_02119_gb300 import build
+    build.build()
+    from paper_2103_02119_gb300 import lbm
+    return lbm
+
+
+def declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L.lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", L.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (lbm_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_params_layout_matches_header(L, tmp_path):
+    fields = [f for f, _ in L.lbm_params._fields_]
+    src = tmp_path / "off.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\nint main(void){\n'
+                   + "".join(f'printf("{f} %zu\\n", offsetof(lbm_params, {f}));\n' for f in fields)
+                   + 'printf("sizeof %zu\\n", sizeof(lbm_params));\nreturn 0;}\n')
+    exe = tmp_path / "off"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True,
+                                                      text=True).stdout.splitlines())
+    for f in fields:
+        assert int(got[f]) == getattr(L.lbm_params, f).offset, f
+    assert int(got["sizeof"]) == ctypes.sizeof(L.lbm_params)
+
+
+def test_params_init_defaults(L):
+    p = L.lbm_params_init()
+    assert (p.nx, p.ny, p.precision, p.periodic_x, p.periodic_y) == (64, 64, 32, 1, 1)
+    assert p.a == 1.0 and abs(p.cs2 - 1 / 3) < 1e-15 and p.rho0 == 1.0
+    assert list(p.omega) == [1.0] * 9
+
+
+BAD = [
+    ("nx", 2, "nx and ny"),
+    ("ny", 0, "nx and ny"),
+    ("a", 0.0, "a must"),
+    ("a", float("nan"), "a must"),
+    ("cs2", 0.3, "cs2"),          # with a = 0.5: cs2 >= a^2
+    ("cs2", -1.0, "cs2"),
+    ("precision", 16, "precision"),
+    ("periodic_x", 2, "periodic"),
+    ("block_x", 48, "block_x"),
+    ("bands", -1, "bands"),
+    ("rho0", -1.0, "rho0"),
+    ("Fx", float("inf"), "force"),
+    ("use_gi_corr", 3, "correction"),
+    ("scheme", 2, "scheme"),
+]
+
+
+@pytest.mark.parametrize("field,value,msg", BAD)
+def test_invalid_params_rejected_on_host(L, field, value, msg):
+    p = L.lbm_params_init()
+    p.a, p.cs2 = 0.5, 0.1
+    setattr(p, field, value)
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_create(p)
+    assert e.value.status == L.LBM_ERR_INVALID
+    assert msg in str(e.value)
+
+
+@pytest.mark.parametrize("j,value", [(3, 0.0), (4, 0.0), (5, 2.5), (0, -0.1)])
+def test_invalid_relaxation_rates(L, j, value):
+    p = L.lbm_params_init()
+    p.omega[j] = value
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_create(p)
+    assert e.value.status == L.LBM_ERR_INVALID
+
+
+def test_null_arguments(L):
+    p = L.lbm_params_init()
+    assert L.lib.lbm_create(ctypes.byref(p), None, None, None) == L.LBM_ERR_INVALID
+    assert L.lib.lbm_create(None, None, None, ctypes.byref(ctypes.c_void_p())) == L.LBM_ERR_INVALID
+    assert "params is NULL" in L.lbm_last_error(None)
+    assert L.lib.lbm_step(None, 1) == L.LBM_ERR_INVALID
+    assert L.lib.lbm_diagnostics(None, None) == L.LBM_ERR_INVALID
+    L.lib.lbm_destroy(None)  # ignored
+    assert L.lib.lbm_step_count(None) == -1

@@ -1,0 +1,253 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 oracle.
+
+Element by element on populations, density and velocity, after several
+steps from a seeded non-equilibrium state, for every boundary type the
+library supports: periodic axes, implicit half-way walls, a moving lid,
+solid masks; grids that span several blocks with ragged tails, tiny grids,
+a > 1, corrections switched off; FP64 and FP32 storage.  Full-size workloads
+are checked in the launch configuration the benchmark uses.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2103_02119_gb300 import workloads as W
+from gpu_common import compare, gpu_of, oracle_of, pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _fields(wl, seed, u_amp=0.02):
+    r, u, v = W.smooth_random_fields(wl.nx, wl.ny, seed, u_amp=u_amp, rho_amp=2e-3)
+    return wl.with_(rho=r, ux=u, uy=v)
+
+
+def configs():
+    c = {}
+    c["tgv_ragged"] = W.taylor_green(300, 67, 0.5, 0.075, 0.02, u0=0.03, seed=1, wavelength=60)
+    c["channel_force"] = _fields(W.poiseuille(ny=40, nx=70, a=0.25, cs2=0.04, nu=0.02, U=0.03), 2)
+    c["cavity_lid"] = _fields(W.cavity(45, 90, 0.5, 0.075, 0.05, 100.0), 3)
+    c["obstacles_periodic"] = W.taylor_green(100, 80, 0.8, 0.2, 0.02, u0=0.02, seed=2).with_(
+        mask=W.random_obstacles(100, 80, seed=3, coverage=0.1))
+    c["obstacles_lid_a025"] = _fields(W.cavity(64, 128, 0.25, 0.01875, 0.03, 200.0), 4).with_(
+        mask=W.random_obstacles(64, 128, seed=5, coverage=0.1))
+    c["tiny_3x3"] = _fields(W.taylor_green(3, 3, 1.0, 1 / 3, 0.05, u0=0.01, seed=6), 6)
+    c["tiny_4x5_lid"] = _fields(W.cavity(4, 5, 0.5, 0.075, 0.02, 10.0), 7)
+    m = np.zeros((7, 5), np.uint8)
+    m[3, 2] = 1
+    c["tiny_5x7_mask"] = _fields(W.taylor_green(5, 7, 0.5, 0.075, 0.05, seed=8), 8).with_(mask=m)
+    c["no_corrections"] = W.taylor_green(96, 50, 0.25, 0.01875, 0.02, u0=0.02, seed=9).with_(
+        use_iso_corr=0, use_gi_corr=0)
+    c["a2_force_xy"] = W.taylor_green(64, 40, 2.0, 1 / 3, 0.05, u0=0.02, seed=10).with_(
+        Fx=2e-5, Fy=-1e-5)
+    return c
+
+
+CONFIGS = configs()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+def test_parity(orc, name, precision):
+    wl = CONFIGS[name]
+    o, g = pair(orc, wl, precision, noise_seed=11, noise_amp=5e-4)
+    compare(o, g, precision)          # the initial state itself
+    o.step(7)
+    g.step(7)
+    compare(o, g, precision)
+    o.step(13)
+    g.step(13)
+    compare(o, g, precision)
+    assert g.step_count == 20 and g.launch_count == 20
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("block_x,bands", [(32, 1), (32, 67), (64, 5), (256, 2), (128, 33)])
+def test_tilings_are_bit_identical(precision, block_x, bands):
+    """The result does not depend on how the step kernel is tiled: every cell
+    computes the same arithmetic whichever block owns it or its halo."""
+    wl = CONFIGS["obstacles_lid_a025"] if bands != 67 else CONFIGS["tgv_ragged"]
+    ref = gpu_of(wl, precision)
+    alt = gpu_of(wl, precision, block_x=block_x, bands=min(bands, wl.ny))
+    ref.step(9)
+    alt.step(9)
+    assert ref.get_state() == alt.get_state()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_config1_poiseuille(orc, precision):
+    """32 x 32 channel, a = 0.5, nu = 0.1, u_max = 0.01, 5000 steps from rest:
+    against the oracle and against the parabola of Sec. 5.1."""
+    wl = W.poiseuille()
+    o, g = oracle_of(orc, wl), gpu_of(wl, precision)
+    o.step(5000)
+    g.step(5000)
+    _, uo, vo = o.moments()
+    rg, ug, vg = g.moments()
+    if precision == 64:
+        assert np.abs(ug - uo).max() <= 1e-12 * np.abs(uo).max()
+        assert np.abs(vg).max() < 1e-14
+    else:
+        assert rel_l2(ug, uo) <= 1e-5
+    H, U = wl.info["H"], wl.info["U"]
+    y = (np.arange(wl.ny) + 0.5) * wl.a
+    ua = (U * (1 - (y - H / 2) ** 2 / (H / 2) ** 2))[:, None]
+    err = np.abs(ug - ua).sum() / (np.abs(ua).sum() * wl.nx)
+    assert err < 3e-3
+
+
+def test_tgv_decay_fp32_vs_fp64(orc):
+    """Taylor-Green decay on the rectangular lattice (config 2 shape, reduced
+    size): FP32 storage tracks the FP64 oracle within 1e-5 on velocity."""
+    wl = W.taylor_green(128, 256, 0.5, 0.075, 0.01, u0=0.02, seed=0)
+    o, g = oracle_of(orc, wl), gpu_of(wl, 32)
+    o.step(1000)
+    g.step(1000)
+    _, uo, vo = o.moments()
+    _, ug, vg = g.moments()
+    assert rel_l2(np.stack([ug, vg]), np.stack([uo, vo])) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_full_size_shear_config2(orc, precision):
+    """2048 x 1024 periodic Taylor-Green field at a = 0.5 with a perturbation,
+    in the default launch configuration, two steps."""
+    wl = W.taylor_green(2048, 1024, 0.5, 0.075, 0.01, u0=0.02, seed=1, wavelength=256)
+    o, g = pair(orc, wl, precision, noise_seed=2, noise_amp=2e-4)
+    o.step(2)
+    g.step(2)
+    compare(o, g, precision)
+
+
+def test_full_size_cavity_config3(orc):
+    """2048 x 8192 lid-driven cavity at a = 0.25 (the benchmark workload),
+    FP32, in the benchmark's launch configuration, two steps from a smooth
+    random state."""
+    wl = _fields(W.cavity(2048, 8192, 0.25, 0.04, 0.05, 1000.0), 12, u_amp=0.03)
+    o, g = pair(orc, wl, 32, noise_seed=13, noise_amp=2e-4)
+    o.step(2)
+    g.step(2)
+    compare(o, g, 32)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_diagnostics_match_oracle_fields(orc, precision):
+    wl = CONFIGS["obstacles_lid_a025"]
+    o, g = pair(orc, wl, precision, noise_seed=3, noise_amp=2e-4)
+    st, d0 = g.diagnostics()
+    assert st == 0 and d0[4] == -1.0 and d0[5] == 0 and d0[6] == 0
+    o.step(10)
+    g.step(10)
+    ro, uo, vo = o.moments()
+    uo_prev, vo_prev = None, None
+    st, d = g.diagnostics()
+    assert st == 0 and d[5] == 0 and d[6] == 10
+    tol = 1e-12 if precision == 64 else 1e-6
+    assert abs(d[0] - math.fsum(ro.ravel())) <= tol * d[0]
+    scale = math.fsum(np.abs(ro * uo).ravel()) + math.fsum(np.abs(ro * vo).ravel())
+    assert abs(d[1] - math.fsum((ro * uo).ravel())) <= tol * scale
+    assert abs(d[2] - math.fsum((ro * vo).ravel())) <= tol * scale
+    en = math.fsum((0.5 * ro * (uo ** 2 + vo ** 2)).ravel())
+    assert abs(d[3] - en) <= 10 * tol * en
+    # residual between two calls 5 steps apart, from the oracle's fields
+    uo_prev, vo_prev = uo, vo
+    o.step(5)
+    g.step(5)
+    _, uo, vo = o.moments()
+    st, d = g.diagnostics()
+    R = math.sqrt(math.fsum(((uo - uo_prev) ** 2 + (vo - vo_prev) ** 2).ravel())) / (
+        5 * math.sqrt(math.fsum((uo ** 2 + vo ** 2).ravel())))
+    assert abs(d[4] - R) <= (1e-9 if precision == 64 else 1e-4) * R
+
+
+def test_streaming_is_a_permutation_mass_bit_exact():
+    """With the collision switched off, a step only moves stored values (pull
+    streaming and stationary bounce-back), so the exactly-summed mass keeps
+    every bit, FP64 and FP32."""
+    for precision in (64, 32):
+        wl = _fields(W.cavity(77, 50, 0.5, 0.075, 0.0, 100.0), 14).with_(
+            mask=W.random_obstacles(77, 50, seed=15))
+        g = gpu_of(wl, precision, scheme=-1)
+        g.set_f(g.get_f() + W.perturbation(77, 50, 16, 1e-3))
+        _, d0 = g.diagnostics()
+        g.step(1001)
+        _, d1 = g.diagnostics()
+        assert d1[0] == d0[0]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_mass_drift_of_full_step(precision):
+    """The collision conserves mass in exact arithmetic; in floating point the
+    global drift per step stays at rounding level."""
+    wl = CONFIGS["obstacles_lid_a025"].with_(wall_u=((0, 0),) * 4)
+    g = gpu_of(wl, precision)
+    _, d0 = g.diagnostics()
+    g.step(200)
+    _, d1 = g.diagnostics()
+    eps = 2.2e-16 if precision == 64 else 1.2e-7
+    assert abs(d1[0] - d0[0]) <= 200 * 0.05 * eps * wl.cells + 4 * eps * d0[0]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_checkpoint_resume_and_determinism(precision):
+    wl = CONFIGS["cavity_lid"]
+    a = gpu_of(wl, precision)
+    a.step(30)
+    snap = a.get_state()
+    a.step(25)
+    end = a.get_state()
+    b = gpu_of(wl, precision)
+    b.set_state(snap)
+    b.step(25)
+    assert b.get_state() == end
+    c = gpu_of(wl, precision)
+    c.step(55)
+    assert c.get_state() == end
+
+
+def test_device_io_matches_host_io():
+    import torch
+    wl = CONFIGS["channel_force"]
+    g = gpu_of(wl, 64)
+    N = wl.cells
+    rho = torch.tensor(wl.rho.ravel(), dtype=torch.float64, device="cuda")
+    ux = torch.tensor(wl.ux.ravel(), dtype=torch.float64, device="cuda")
+    uy = torch.tensor(wl.uy.ravel(), dtype=torch.float64, device="cuda")
+    g.init_fields(rho, ux, uy)
+    g.step(5)
+    out = [torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3)]
+    from paper_2103_02119_gb300 import lbm
+    lbm.lbm_moments(g.h, N, *out)
+    torch.cuda.synchronize()
+    host = g.moments()
+    for d_, h_ in zip(out, host):
+        assert np.array_equal(d_.cpu().numpy().reshape(h_.shape), h_)
+    fd = torch.empty(9 * N, dtype=torch.float64, device="cuda")
+    lbm.lbm_get_f(g.h, N, fd)
+    torch.cuda.synchronize()
+    assert np.array_equal(fd.cpu().numpy().reshape(9, wl.ny, wl.nx), g.get_f())
+
+
+def test_nonfinite_state_is_reported_and_recoverable():
+    from paper_2103_02119_gb300 import lbm
+    wl = CONFIGS["tgv_ragged"]
+    g = gpu_of(wl, 32)
+    f = g.get_f()
+    bad = f.copy()
+    bad[:, 10, 20] = np.nan
+    g.set_f(bad)
+    st, d = g.diagnostics()
+    assert st == lbm.LBM_ERR_UNSTABLE and d[5] >= 1 and math.isnan(d[0])
+    assert "non-finite" in lbm.lbm_last_error(g.h)
+    g.set_f(f)
+    st, d = g.diagnostics()
+    assert st == lbm.LBM_OK and d[5] == 0
+
+
+def test_state_size_mismatch_is_rejected():
+    from paper_2103_02119_gb300 import lbm
+    g = gpu_of(CONFIGS["tiny_3x3"], 32)
+    with pytest.raises(lbm.LbmError) as e:
+        g.set_state(b"\0" * 8)
+    assert e.value.status == lbm.LBM_ERR_STATE
