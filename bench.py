@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--block-x", type=int, default=0)
     ap.add_argument("--bands", type=int, default=0)
@@ -309,7 +310,7 @@ def main():
                 "frac": achieved / peak, "traffic": profiled_traffic(args.precision, cells),
                 "peak_kind": peak_kind, "kernel": f"rc_step_kernel<fp{args.precision}>",
                 "algorithmic_bytes_per_cell": BYTES_PER_CELL[args.precision]}
-    e2e_res = e2e(lat, wl, torch, args.e2e_chunk, args.e2e_steps)
+    e2e_res = None if args.no_e2e else e2e(lat, wl, torch, args.e2e_chunk, args.e2e_steps)
 
     fp64 = None
     if not args.no_fp64 and args.precision == 32:
