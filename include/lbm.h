@@ -149,6 +149,27 @@ lbm_status lbm_set_f(lbm_handle* h, const double* f, int on_device);
  * Returns LBM_ERR_UNSTABLE (with out filled) when out[5] > 0. */
 lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]);
 
+/* The values of lbm_diagnostics, for callers that cannot allocate device
+ * memory: a process whose free device memory is already reserved by another
+ * allocator (a framework's caching allocator, say), so that cudaMalloc would
+ * fail, or a monitoring loop that must not pay cudaMalloc's implicit device
+ * synchronisation.  lbm_diagnostics allocates its residual reference field
+ * on its first call; this entry point allocates nothing.  Its scratch -- the
+ * per-block partial sums and the reference velocity field of the residual --
+ * is one fixed device array inside the library (about 16.1 MiB) that every
+ * GPU loading the library holds until the process exits.
+ * Limit: lattices of at most 1048576 (2^20) cells; larger ones get
+ * LBM_ERR_INVALID and a message naming the limit.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.
+ * All calls on a device share the array: out[4] is measured against the
+ * velocity of the previous lbm_diagnostics_noalloc call, and is -1 unless
+ * that call was on the same handle at a smaller step count (init and set
+ * calls in between are not detected).  Calls that overlap on the GPU (other
+ * streams, other threads) race on the array.
+ * The paper has no counterpart to this entry point: it is library plumbing. */
+lbm_status lbm_diagnostics_noalloc(lbm_handle* h, double out[LBM_DIAG_COUNT]);
+
 /* Size in bytes of the raw state (checkpoint) of a handle. */
 size_t lbm_state_bytes(const lbm_handle* h);
 

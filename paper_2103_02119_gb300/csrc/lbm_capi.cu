@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -14,6 +16,11 @@
 using lbm::AuxParams;
 using lbm::DiagPartial;
 using lbm::KParams;
+
+static unsigned long long next_handle_serial() {
+    static std::atomic<unsigned long long> n{0};
+    return ++n;
+}
 
 struct lbm_handle {
     lbm_params p{};
@@ -35,6 +42,7 @@ struct lbm_handle {
     int bx = 0, nbands = 0;
     int64_t steps = 0, launches = 0;
     char err[512] = {0};
+    unsigned long long serial = next_handle_serial();
 };
 
 namespace {
@@ -597,3 +605,104 @@ int64_t lbm_launch_count(const lbm_handle* h) { return h ? h->launches : -1; }
 const char* lbm_last_error(const lbm_handle* h) { return h ? h->err : g_err; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Diagnostics that allocate nothing.
+//
+// lbm_diagnostics allocates its residual reference field (cudaMalloc) on its
+// first call.  lbm_diagnostics_noalloc computes the same values with its
+// scratch -- the per-block partial sums and the reference velocity field of
+// the residual -- in one fixed device array of this library instead.  The
+// array is a file-scope static __device__ object: every GPU that loads the
+// library holds it (kNoAllocScratchBytes, about 16.1 MiB) until the process
+// exits, and every call on a device shares it.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr long long kNoAllocMaxCells = 1LL << 20;  // lattice size limit
+constexpr int kNoAllocMaxBlocks = 1024;            // reduction blocks limit
+constexpr size_t kNoAllocPartBytes =
+    ((kNoAllocMaxBlocks + 1) * sizeof(DiagPartial) + 255) / 256 * 256;
+constexpr size_t kNoAllocScratchBytes =
+    kNoAllocPartBytes + 2 * (size_t)kNoAllocMaxCells * sizeof(double);
+constexpr int kNoAllocMaxDevices = 128;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+// Host-side record per device: the device address of the array (its name in
+// host code is only a stand-in, never a device address), and which handle's
+// velocity field the reference part currently holds.
+struct NoAllocDevice {
+    unsigned char* base = nullptr;
+    unsigned long long owner = 0;  // serial of the handle of the last call
+    int64_t step = 0;              // its step counter at that call
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc[kNoAllocMaxDevices];
+}  // namespace
+
+extern "C" lbm_status lbm_diagnostics_noalloc(lbm_handle* h, double out[LBM_DIAG_COUNT]) {
+    if (!h || !out) return LBM_ERR_INVALID;
+    if (h->N > kNoAllocMaxCells) {
+        set_err(h, "lbm_diagnostics_noalloc: the lattice has %lld cells, its fixed scratch "
+                   "holds at most %lld; use lbm_diagnostics",
+                (long long)h->N, (long long)kNoAllocMaxCells);
+        return LBM_ERR_INVALID;
+    }
+    if (h->diag_blocks > kNoAllocMaxBlocks) {
+        set_err(h, "lbm_diagnostics_noalloc: %d reduction blocks exceed the fixed scratch "
+                   "(%d); use lbm_diagnostics",
+                h->diag_blocks, kNoAllocMaxBlocks);
+        return LBM_ERR_INVALID;
+    }
+    int dev = 0;
+    CK(h, cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_err(h, "lbm_diagnostics_noalloc: device %d is beyond the %d supported", dev,
+                kNoAllocMaxDevices);
+        return LBM_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDevice& d = g_noalloc[dev];
+    if (!d.base) {  // once per device, with that device current
+        void* ptr = nullptr;
+        CK(h, cudaGetSymbolAddress(&ptr, g_noalloc_scratch), "cudaGetSymbolAddress");
+        d.base = (unsigned char*)ptr;
+    }
+    DiagPartial* part = (DiagPartial*)d.base;
+    double* uref = (double*)(d.base + kNoAllocPartBytes);
+    // The reference field is valid only if this handle made the last call on
+    // this device and has advanced since; nothing else needs clearing (every
+    // block writes its own partial and the final sum overwrites its slot).
+    const int have = d.owner == h->serial && h->steps > d.step;
+    const AuxParams a = aux(h);
+    cudaError_t e = h->p.precision == 64
+                        ? lbm::launch_diag<double>((const double*)h->f[h->cur], a, uref, have,
+                                                   part, h->diag_blocks, h->stream)
+                        : lbm::launch_diag<float>((const float*)h->f[h->cur], a, uref, have,
+                                                  part, h->diag_blocks, h->stream);
+    CK(h, e, "diagnostics kernels");
+    DiagPartial r;
+    CK(h, cudaMemcpyAsync(&r, part + h->diag_blocks, sizeof(r), cudaMemcpyDeviceToHost,
+                          h->stream),
+       "cudaMemcpyAsync(D2H)");
+    CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    out[0] = fixed_to_double(r.limb) + (double)h->n_fluid * h->p.rho0;
+    out[1] = r.mx;
+    out[2] = r.my;
+    out[3] = r.en;
+    out[4] = (have && r.ures > 0.0)
+                 ? std::sqrt(r.dres) / ((double)(h->steps - d.step) * std::sqrt(r.ures))
+                 : -1.0;
+    out[5] = (double)r.nonfinite;
+    out[6] = (double)h->steps;
+    d.owner = h->serial;
+    d.step = h->steps;
+    if (r.nonfinite > 0) {
+        out[0] = NAN;
+        set_err(h, "%lld fluid cells hold non-finite values", (long long)r.nonfinite);
+        return LBM_ERR_UNSTABLE;
+    }
+    return LBM_OK;
+}

@@ -77,6 +77,7 @@ def _load():
     L.lbm_get_f.argtypes = [_P, _P, ctypes.c_int]
     L.lbm_set_f.argtypes = [_P, _P, ctypes.c_int]
     L.lbm_diagnostics.argtypes = [_P, _D]
+    L.lbm_diagnostics_noalloc.argtypes = [_P, _D]
     L.lbm_state_bytes.argtypes = [_P]
     L.lbm_state_bytes.restype = ctypes.c_size_t
     L.lbm_get_state.argtypes = [_P, _P, ctypes.c_size_t]
@@ -206,6 +207,15 @@ def lbm_diagnostics(h):
     """Returns (status, out[7]); LBM_ERR_UNSTABLE is reported, not raised."""
     out = (ctypes.c_double * LBM_DIAG_COUNT)()
     st = lib.lbm_diagnostics(h, out)
+    if st not in (LBM_OK, LBM_ERR_UNSTABLE):
+        _check(st, h)
+    return st, np.array(out[:], dtype=np.float64)
+
+
+def lbm_diagnostics_noalloc(h):
+    """As lbm_diagnostics, without allocating (fixed in-library scratch)."""
+    out = (ctypes.c_double * LBM_DIAG_COUNT)()
+    st = lib.lbm_diagnostics_noalloc(h, out)
     if st not in (LBM_OK, LBM_ERR_UNSTABLE):
         _check(st, h)
     return st, np.array(out[:], dtype=np.float64)
