@@ -49,6 +49,9 @@ typedef enum {
     LBM_ERR_OOM = -2,      /* a device or host allocation failed              */
     LBM_ERR_CUDA = -3,     /* a CUDA call failed (see lbm_last_error)          */
     LBM_ERR_UNSTABLE = -4, /* lbm_diagnostics found non-finite fluid cells     */
+    LBM_ERR_TIMEOUT = -5,  /* a step kernel gave up waiting for its staged data
+                              (reported by lbm_diagnostics; the state is not
+                              valid after it)                                  */
     LBM_ERR_STATE = -6     /* state buffer of the wrong size                   */
 } lbm_status;
 
@@ -146,7 +149,9 @@ lbm_status lbm_set_f(lbm_handle* h, const double* f, int on_device);
  *          there is no previous call (or n == m)
  *   out[5] number of fluid cells with a non-finite rho or u
  *   out[6] step counter n
- * Returns LBM_ERR_UNSTABLE (with out filled) when out[5] > 0. */
+ * Returns LBM_ERR_UNSTABLE (with out filled) when out[5] > 0, and
+ * LBM_ERR_TIMEOUT when a step kernel since lbm_create gave up a bounded wait
+ * for its staged data. */
 lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]);
 
 /* The values of lbm_diagnostics, for callers that cannot allocate device

@@ -10,7 +10,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 #include "lbm_launch.h"
 
 using lbm::AuxParams;
@@ -25,7 +25,8 @@ static unsigned long long next_handle_serial() {
 struct lbm_handle {
     lbm_params p{};
     int pitch = 0;
-    long long plane = 0;       // elements per population plane
+    long long plane = 0;       // element stride between population planes
+    int rstride = 0;           // element stride between rows of a plane
     long long N = 0;           // nx * ny
     long long n_fluid = 0;
     cudaStream_t stream = nullptr;
@@ -38,6 +39,7 @@ struct lbm_handle {
     double* stage = nullptr;   // host <-> device staging (doubles)
     size_t stage_elems = 0;
     DiagPartial* part = nullptr;
+    int* status = nullptr;     // device word set by a step kernel that timed out
     int diag_blocks = 0;
     int bx = 0, nbands = 0;
     int64_t steps = 0, launches = 0;
@@ -48,6 +50,9 @@ struct lbm_handle {
 namespace {
 
 thread_local char g_err[512] = "no error";
+
+// Population layout of every handle (see lbm_device.cuh).
+constexpr bool kRowInterleaved = false;
 
 void set_err(lbm_handle* h, const char* fmt, ...) {
     char* dst = h ? h->err : g_err;
@@ -69,7 +74,9 @@ lbm_status cuda_fail(lbm_handle* h, cudaError_t e, const char* what) {
     } while (0)
 
 size_t elem_size(const lbm_handle* h) { return h->p.precision == 64 ? 8 : 4; }
-size_t buf_bytes(const lbm_handle* h) { return 9 * (size_t)h->plane * elem_size(h); }
+size_t buf_bytes(const lbm_handle* h) {
+    return 9 * (size_t)h->pitch * (size_t)h->p.ny * elem_size(h);
+}
 
 bool is_fin(double v) { return std::isfinite(v); }
 
@@ -128,6 +135,7 @@ KParams<T> kparams(const lbm_handle* h) {
     k.ny = q.ny;
     k.pitch = h->pitch;
     k.plane = h->plane;
+    k.rstride = h->rstride;
     k.px = q.periodic_x;
     k.py = q.periodic_y;
     k.moving = 0;
@@ -171,6 +179,7 @@ KParams<T> kparams(const lbm_handle* h) {
     k.hFy = T(0.5 * q.Fy);
     k.lmask = h->lmask;
     k.collide = q.scheme == 0;
+    k.status = h->status;
     return k;
 }
 
@@ -180,6 +189,7 @@ AuxParams aux(const lbm_handle* h) {
     a.ny = h->p.ny;
     a.pitch = h->pitch;
     a.plane = h->plane;
+    a.rstride = h->rstride;
     a.px = h->p.periodic_x;
     a.py = h->p.periodic_y;
     a.a = h->p.a;
@@ -306,7 +316,14 @@ lbm_status lbm_create(const lbm_params* p, const uint8_t* solid_mask, void* cuda
     h->p = *p;
     h->stream = (cudaStream_t)cuda_stream;
     h->pitch = (p->nx + 31) / 32 * 32;
-    h->plane = (long long)h->pitch * p->ny;
+    // plane-major layout [9][ny][pitch]; kRowInterleaved stores [ny][9][pitch]
+    if (kRowInterleaved) {
+        h->plane = h->pitch;
+        h->rstride = 9 * h->pitch;
+    } else {
+        h->plane = (long long)h->pitch * p->ny;
+        h->rstride = h->pitch;
+    }
     h->N = (long long)p->nx * p->ny;
     h->n_fluid = h->N;
 
@@ -337,19 +354,29 @@ lbm_status lbm_create(const lbm_params* p, const uint8_t* solid_mask, void* cuda
     CKC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
     h->diag_blocks = 2 * sms;
     CKC(cudaMalloc(&h->part, sizeof(DiagPartial) * (h->diag_blocks + 1)), "cudaMalloc(diagnostics)");
+    CKC(cudaMalloc(&h->status, sizeof(int)), "cudaMalloc(status)");
+    CKC(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "cudaMemset");
 
     // Step kernel launch shape: one block per BX columns and per band of
     // rows, sized so that every block is resident at once (one wave).
+    const bool f64 = p->precision == 64;
+    auto seg_width = [&](int b) {
+        return f64 ? lbm::step_segment_width<double>(b) : lbm::step_segment_width<float>(b);
+    };
     int bx = p->block_x;
-    if (bx == 0) bx = p->nx <= 32 ? 32 : p->nx <= 64 ? 64 : p->nx <= 128 ? 128 : 256;
+    if (bx == 0) bx = p->nx <= seg_width(32) ? 32 : p->nx <= seg_width(64) ? 64 : 128;
     h->bx = bx;
-    const int nseg = (p->nx + bx - 1) / bx;
+    const int nseg = (p->nx + seg_width(bx) - 1) / seg_width(bx);
     int nb = p->bands;
     if (nb == 0) {
+        // Short bands (about 14 rows) keep the blocks that run at the same
+        // time on nearby rows; enough of them to fill every SM, but bands of
+        // at least 6 rows so that the two extra rows a band reads stay cheap.
         const int occ = p->precision == 64 ? lbm::step_occupancy<double>(bx, solid_mask != nullptr)
                                            : lbm::step_occupancy<float>(bx, solid_mask != nullptr);
-        nb = (occ * sms) / nseg;
-        if (nb > p->ny / 4) nb = p->ny / 4;
+        const int fill = (occ * sms + nseg - 1) / nseg;
+        nb = p->ny / 14;
+        if (nb < fill) nb = fill < p->ny / 6 ? fill : p->ny / 6;
         if (nb < 1) nb = 1;
     }
     if (nb > p->ny) nb = p->ny;
@@ -370,6 +397,7 @@ void lbm_destroy(lbm_handle* h) {
     if (h->uprev) cudaFree(h->uprev);
     if (h->stage) cudaFree(h->stage);
     if (h->part) cudaFree(h->part);
+    if (h->status) cudaFree(h->status);
     delete h;
 }
 
@@ -551,7 +579,14 @@ lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]) {
     DiagPartial r;
     CK(h, cudaMemcpyAsync(&r, h->part + h->diag_blocks, sizeof(r), cudaMemcpyDeviceToHost, h->stream),
        "cudaMemcpyAsync(D2H)");
+    int kstatus = 0;
+    CK(h, cudaMemcpyAsync(&kstatus, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+       "cudaMemcpyAsync(D2H)");
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (kstatus) {
+        set_err(h, "a step kernel gave up waiting for its staged data (status %d)", kstatus);
+        return LBM_ERR_TIMEOUT;
+    }
     out[0] = fixed_to_double(r.limb) + (double)h->n_fluid * h->p.rho0;
     out[1] = r.mx;
     out[2] = r.my;

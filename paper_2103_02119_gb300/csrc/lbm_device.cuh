@@ -1,8 +1,11 @@
 // lbm_device.cuh -- device-side building blocks of the RC-LBM step
 // (Yahia & Premnath, arXiv 2103.02119, Sec. 4), for FP32 and FP64.
 //
-// Storage: structure of arrays, nine planes of pitch*ny values (x fastest,
-// rows padded to `pitch`), holding deviations fhat_i = f_i - w_i rho0 from
+// Storage: nine population planes of rows padded to `pitch` values (x
+// fastest); population i of cell (x, y) sits at i * plane + y * rstride + x,
+// so one layout keeps each plane contiguous (plane = pitch * ny,
+// rstride = pitch) and the other interleaves the nine planes row by row
+// (plane = pitch, rstride = 9 * pitch).  The values are deviations fhat_i = f_i - w_i rho0 from
 // the rest equilibrium.  The stored state of a time step is the
 // post-collision field f~ (pull scheme): the next step streams by gathering
 // f_i(x) = f~_i(x - e_i) (Sec. 4, streaming step), and a link whose source
@@ -30,8 +33,9 @@ __host__ __device__ constexpr int opp(int i) {
 // Kernel parameters, converted once on the host to the arithmetic type T.
 template <typename T>
 struct KParams {
-    int nx, ny, pitch;
-    long long plane;          // elements per population plane (pitch * ny)
+    int nx, ny, pitch;        // pitch: padded row length (also of the link mask)
+    long long plane;          // element stride between population planes
+    int rstride;              // element stride between rows of a plane
     int px, py;               // periodic along x / y
     int moving;               // some wall moves
     int collide;              // 0: streaming and bounce-back only
@@ -45,12 +49,14 @@ struct KParams {
     T Fx, Fy, hFx, hFy;       // force and half force
     T wall_u[4][2];
     const uint8_t* __restrict__ lmask;  // per-cell link mask (nullable)
+    int* status;                        // bit 0: a bounded wait ran out
 };
 
 // Host/device double-precision parameters for the auxiliary kernels.
 struct AuxParams {
     int nx, ny, pitch;
     long long plane;
+    int rstride;
     int px, py;
     double a, cs2, rho0, Fx, Fy;
     double wrest[9];          // rest weights times rho0
@@ -81,8 +87,8 @@ __device__ __forceinline__ void pull(const S* __restrict__ fin, const P& p, int 
     const int ym = y == 0 ? p.ny - 1 : y - 1;
     const int yp = y == p.ny - 1 ? 0 : y + 1;
     const long long pl = p.plane;
-    const long long rc = (long long)y * p.pitch, rm = (long long)ym * p.pitch,
-                    rp = (long long)yp * p.pitch;
+    const long long rc = (long long)y * p.rstride, rm = (long long)ym * p.rstride,
+                    rp = (long long)yp * p.rstride;
     const long long c = rc + x;
     f[0] = __ldg(fin + c);
     f[1] = __ldg(fin + ((sb & 1u) ? 3 * pl + c : 1 * pl + rc + xm));
@@ -94,6 +100,11 @@ __device__ __forceinline__ void pull(const S* __restrict__ fin, const P& p, int 
     f[7] = __ldg(fin + ((sb & 64u) ? 5 * pl + c : 7 * pl + rp + xp));
     f[8] = __ldg(fin + ((sb & 128u) ? 6 * pl + c : 8 * pl + rp + xm));
 }
+
+// Reciprocal used by the collision: FP32 takes the hardware approximation
+// (at most 2 ulp off, below the FP32 storage rounding), FP64 an IEEE division.
+__device__ __forceinline__ float rcp(float v) { return __fdividef(1.0f, v); }
+__device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
 
 // 1-D three-velocity Maxwell-matched factors of the equilibrium
 // f_i^eq = rho phi_x(e_ix, u_x) phi_y(e_iy, u_y) (the tensor-product form of
@@ -130,7 +141,7 @@ __device__ __forceinline__ T collide(const KParams<T>& p, T f[9], T d, T dxr, T 
     const T rho = p.rho0 + d;
     const T jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
     const T jy = p.a * ((f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]));
-    const T ir = T(1) / rho;
+    const T ir = rcp(rho);
     const T ux = (jx + p.hFx) * ir;
     const T uy = (jy + p.hFy) * ir;
     const T a = p.a, a2 = p.a2, cs2 = p.cs2;
@@ -183,7 +194,7 @@ __device__ __forceinline__ T collide(const KParams<T>& p, T f[9], T d, T dxr, T 
     const T gx = p.g1h * ux * dxr, gy = p.g2h * uy * dyr;
     const T R3 = N3 + gx + gy;
     const T R4 = N4 + gx - gy;
-    const T idet = T(1) / (rho * (b1 * c2 - b2 * c1));
+    const T idet = rcp(rho * (b1 * c2 - b2 * c1));
     const T dxux = (c2 * R3 - b2 * R4) * idet;
     const T dyuy = (b1 * R4 - c1 * R3) * idet;
 

@@ -22,6 +22,9 @@ cudaError_t launch_step(const T* fin, T* fout, const KParams<T>& p, int bx, int 
                         cudaStream_t s);
 template <typename T>
 int step_occupancy(int bx, bool mask);
+// columns of lattice one block of bx threads of the step kernel covers
+template <typename T>
+int step_segment_width(int bx);
 
 // f = f^eq(rho, u) (device inputs, nullable), written in pull-scheme form.
 template <typename T>

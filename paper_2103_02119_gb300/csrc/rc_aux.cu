@@ -37,7 +37,7 @@ __global__ void init_kernel(T* __restrict__ f, const AuxParams p, const double* 
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % p.nx), y = (int)(c / p.nx);
-        const long long o = (long long)y * p.pitch + x;
+        const long long o = (long long)y * p.rstride + x;
         const unsigned sb = link_bits<MASK>(p, x, y);
         if (sb == 0xFFu) {
             for (int i = 0; i < 9; ++i) f[i * p.plane + o] = T(0);
@@ -66,7 +66,7 @@ __global__ void set_f_kernel(T* __restrict__ f, const AuxParams p,
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % p.nx), y = (int)(c / p.nx);
-        const long long o = (long long)y * p.pitch + x;
+        const long long o = (long long)y * p.rstride + x;
         const unsigned sb = link_bits<MASK>(p, x, y);
         if (sb == 0xFFu) {
             for (int i = 0; i < 9; ++i) f[i * p.plane + o] = T(0);

@@ -24,11 +24,12 @@ LBM_ERR_INVALID = -1
 LBM_ERR_OOM = -2
 LBM_ERR_CUDA = -3
 LBM_ERR_UNSTABLE = -4
+LBM_ERR_TIMEOUT = -5
 LBM_ERR_STATE = -6
 LBM_DIAG_COUNT = 7
 DIAG_NAMES = ("mass", "mom_x", "mom_y", "energy", "residual", "nonfinite", "step")
 _STATUS = {0: "LBM_OK", -1: "LBM_ERR_INVALID", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA",
-           -4: "LBM_ERR_UNSTABLE", -6: "LBM_ERR_STATE"}
+           -4: "LBM_ERR_UNSTABLE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE"}
 
 
 class LbmError(RuntimeError):
