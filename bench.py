@@ -172,6 +172,19 @@ def profiled_traffic(precision, cells):
     return e["dram_bytes_per_cell"] * cells
 
 
+# ------------------------------------------------------- multi-rank timing --
+
+def max_over_ranks(secs: float, dist=None) -> float:
+    """Wall time of the job: the slowest rank's time (every rank runs a
+    replica of the workload; there is no data-path collective)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return secs
+    import torch
+    t = torch.tensor([secs], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------- GPU timing --
 
 def time_steps(lat, torch, steps, warmup, barrier):
@@ -296,10 +309,7 @@ def main():
                                 block_x=args.block_x, bands=args.bands)
     with ClockSampler(local) as clk:
         secs, launches = time_steps(lat, torch, args.steps, args.warmup, barrier)
-    if dist is not None:
-        t = torch.tensor([secs], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
+    secs = max_over_ranks(secs, dist)
     cells = wl.cells
     value = world * cells * args.steps / secs / 1e6
     per_launch = secs / args.steps
