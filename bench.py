@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-sweep measurements")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--ttr-count", type=int, default=64)
+    ap.add_argument("--ttr-max-steps", type=int, default=60000)
     ap.add_argument("--block-x", type=int, default=0)
     ap.add_argument("--bands", type=int, default=0)
     return ap.parse_args()
@@ -233,6 +239,97 @@ def e2e(lat, wl, torch, chunk, reps):
                     f"lbm_step({chunk}), lbm_moments to pinned host rho/u"}
 
 
+# ------------------------------------------------------------ batched sweep --
+
+def batch_throughput(torch, count, steps):
+    """One persistent launch per step over `count` uneven lattices, against
+    the same lattices advanced one after another with the single-lattice
+    step (one launch per lattice and step)."""
+    from paper_2103_02119_gb300 import workloads as W
+    from paper_2103_02119_gb300.lbm import Batch, Lattice
+    stream = torch.cuda.current_stream()
+    ws = W.batch_sweep(count, seed=0)
+    cells = sum(w.cells for w in ws)
+    b = Batch(ws, stream=stream)
+    shape = b.tune(trial_steps=10)
+    b.step(4)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = b.launch_count
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / 1e3
+    launches = b.launch_count - l0
+    b.close()
+    lats = [Lattice.from_workload(w, precision=32, stream=stream) for w in ws]
+    for lat in lats:
+        lat.step(2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for lat in lats:
+        lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ts = e0.elapsed_time(e1) / 1e3
+    for lat in lats:
+        lat.close()
+    return {"workload": f"{count} channel/cavity lattices, nx, ny log-uniform in [64, 1024], "
+                        "a in [0.2, 1], Re log-uniform in [100, 5000], <= 10% obstacles, "
+                        "seed 0", "cells": cells, "steps": steps,
+            "shape": {"block_x": shape[0], "rows_per_band": shape[1]},
+            "batched_mlups": cells * steps / tb / 1e6, "batched_launches": launches,
+            "sequential_mlups": cells * steps / ts / 1e6,
+            "sequential_launches": count * steps, "speedup": ts / tb}
+
+
+def batch_time_to_residual(torch, count, max_steps, tol=1e-8, check=100):
+    """Wall time until every lattice of a reduced sweep has a steady
+    residual <= tol: the batch (autotune + run with retirement) against the
+    same lattices run one after another (lbm_step / lbm_diagnostics loop)."""
+    import numpy as np
+    from paper_2103_02119_gb300 import workloads as W
+    from paper_2103_02119_gb300.lbm import Batch, Lattice
+    stream = torch.cuda.current_stream()
+    ws = W.batch_sweep(count, seed=1, n_range=(16, 32), re_range=(10.0, 100.0))
+    b = Batch(ws, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.tune(trial_steps=5)
+    st, res = b.run(tol, check_every=check, max_steps=max_steps)
+    tb = time.perf_counter() - t0
+    nb = int(sum(1 for r in res if 0 <= r <= tol))
+    steps_b = [b.step_count(k) for k in range(count)]
+    b.close()
+    ts = 0.0
+    ns, steps_s = 0, []
+    for w in ws:
+        lat = Lattice.from_workload(w, precision=32, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.diagnostics()
+        n, R = 0, -1.0
+        while n < max_steps:
+            lat.step(check)
+            n += check
+            _, d = lat.diagnostics()
+            R = d[4]
+            if not np.isfinite(R) or 0 <= R <= tol:
+                break
+        ts += time.perf_counter() - t0
+        ns += int(0 <= R <= tol)
+        steps_s.append(n)
+        lat.close()
+    return {"sample": f"{count} lattices of the same sweep recipe with nx, ny in [16, 32] "
+                      "and Re in [10, 100] (seed 1), so that all converge in a bounded run",
+            "tol": tol, "check_every": check, "max_steps": max_steps,
+            "batched_s": tb, "batched_converged": nb, "batched_max_steps": max(steps_b),
+            "sequential_s": ts, "sequential_converged": ns,
+            "sequential_max_steps": max(steps_s), "speedup": ts / tb}
+
+
 # -------------------------------------------------------------- oracle arm --
 
 def oracle_mlups(wl, rows, seconds, warmup_steps=0, steps=None):
@@ -336,6 +433,12 @@ def main():
     else:
         lat.close()
 
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = batch_throughput(torch, args.batch_count, args.batch_steps)
+        batch["time_to_residual"] = batch_time_to_residual(torch, args.ttr_count,
+                                                           args.ttr_max_steps)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         mlups, threads, steps, desc, _ = oracle_mlups(wl, wl.ny, args.cpu_seconds)
@@ -350,7 +453,7 @@ def main():
             "dtype": f"f{args.precision}", "data": "synthetic",
             "config": workload_config(args, wl), "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches,
-            "clocks": clk.summary(), "fp64": fp64,
+            "clocks": clk.summary(), "fp64": fp64, "batch": batch,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

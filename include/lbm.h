@@ -85,9 +85,11 @@ typedef struct {
                               0 = automatic, else one of 32, 64, 128, 256        */
     int32_t bands;         /* step kernel tuning: number of row bands,
                               0 = automatic                                     */
-    int32_t scheme;        /* 0: RC-LBM collision (Sec. 4); -1: no collision
-                              (streaming and bounce-back only, a test mode in
-                              which a step is a permutation of the state)       */
+    int32_t scheme;        /* 0: RC-LBM collision (Sec. 4); 1: raw-moment
+                              collision (RNR-LBM, Sec. 3: Eq. 10-13 with the
+                              same corrections); -1: no collision (streaming
+                              and bounce-back only, a test mode in which a
+                              step is a permutation of the state)               */
 } lbm_params;
 
 /* Fill *p with defaults: 64 x 64 periodic, a = 1, cs2 = 1/3, all omega 1,
@@ -129,6 +131,25 @@ lbm_status lbm_set_force(lbm_handle* h, double Fx, double Fy);
  * stream; device outputs (on_device != 0) are written asynchronously. */
 lbm_status lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy,
                        int on_device);
+
+/* Local strain rates and viscous stress of the current state, in FP64, as
+ * the next collision sees it (Sec. 2.2): d_x u_x and d_y u_y from the
+ * second-order non-equilibrium raw moments (Eq. 34-35, 37-38, 40), the
+ * off-diagonal rate d_y u_x + d_x u_y from m5 - rho ux uy over
+ * D1 = -rho cs2 / omega[5] (Eq. 36, 39: its left side is read as the
+ * off-diagonal rate, as Eq. 21 gives it), with the density gradient of the
+ * step (central differences, spacing 2 and 2a, a wall or solid neighbour
+ * taking the cell's own density); and the viscous stress of the recovered
+ * Navier-Stokes equations (Eq. 30-33):
+ *   txx = rho [nu (2 d_x u_x - div u) + zeta div u], tyy likewise,
+ *   txy = rho nu' (d_y u_x + d_x u_y),
+ * nu = cs2 (1/omega[4] - 1/2), nu' = cs2 (1/omega[5] - 1/2),
+ * zeta = cs2 (1/omega[3] - 1/2).  Each output is nx*ny doubles, nullable;
+ * solid cells give 0.  Host or device memory as for lbm_moments (host
+ * outputs synchronise the stream).  Uses a staging buffer of the handle
+ * (7 nx ny doubles for host outputs, nx ny for device outputs). */
+lbm_status lbm_stress(lbm_handle* h, double* dxux, double* dyuy, double* sxy,
+                      double* txx, double* tyy, double* txy, int on_device);
 
 /* Distributions f_i(x, t) of the current state (after streaming), as
  * doubles, 9*nx*ny in plane-major order f[i*nx*ny + y*nx + x]; solid cells
@@ -194,6 +215,112 @@ int64_t lbm_launch_count(const lbm_handle* h);
 /* Message of the last error on h (or of the last failed lbm_create when h is
  * NULL); never NULL.  Not thread-safe. */
 const char* lbm_last_error(const lbm_handle* h);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent FP32 lattices of uneven size, aspect ratio and
+ * parameters advanced together.  Each lattice runs exactly the scheme of
+ * lbm_step (Sec. 4, with the walls of Sec. 5.1): a lattice of a batch and an
+ * lbm_handle created from the same parameters and mask go through the same
+ * states bit for bit.  The paper solves one lattice at a time; batching, the
+ * steady-state residual loop and the autotuner are library plumbing with no
+ * counterpart there.
+ *
+ * Every step of a batch is one launch of a persistent kernel that walks a
+ * device work list of (lattice, column segment, band of rows) items of the
+ * active lattices; runs of 50 steps replay a captured CUDA graph.  Lattices
+ * can be retired (made inactive) and brought back; an inactive lattice keeps
+ * its state and is not stepped.  Conventions as for lbm_handle; work is
+ * issued on the stream given to lbm_batch_create.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch;
+
+/* Create `count` (1 .. 2^20) lattices.  params: count parameter sets as for
+ * lbm_create, each with precision 32 and fewer than 2^31 stored values per
+ * buffer (9 x ny x nx rounded up to 32); block_x and bands are ignored (the
+ * batch has one launch shape, see lbm_batch_set_shape).  solid_masks:
+ * nullable, else count pointers, each nullable or nx*ny bytes as for
+ * lbm_create (copied).  Every lattice starts at rest and active.  Device
+ * memory: two population buffers, a link mask and a residual reference field
+ * (2 nx ny doubles) per lattice, in one allocation each.
+ * Errors: LBM_ERR_INVALID (naming the first bad lattice), LBM_ERR_OOM,
+ * LBM_ERR_CUDA; *out is NULL on failure. */
+lbm_status lbm_batch_create(const lbm_params* params, int count,
+                            const uint8_t* const* solid_masks, void* cuda_stream,
+                            lbm_batch** out);
+
+/* Destroy a batch and free its device memory.  NULL is ignored. */
+void lbm_batch_destroy(lbm_batch* b);
+
+/* Number of lattices, or -1 for NULL. */
+int lbm_batch_count(const lbm_batch* b);
+
+/* lbm_init_fields for lattice k (0 <= k < count): equilibrium state of
+ * Sec. 4 from rho, ux, uy (nullable; host or device).  Resets its step
+ * counter and residual reference. */
+lbm_status lbm_batch_init_fields(lbm_batch* b, int k, const double* rho,
+                                 const double* ux, const double* uy, int on_device);
+
+/* Advance every active lattice by nsteps >= 0 steps.  Asynchronous. */
+lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
+
+/* Steady residual of every lattice, synchronous: res (count doubles,
+ * nullable) gets, for each active lattice, the residual of lbm_diagnostics'
+ * out[4] (FP64 sums over its fluid cells) against its velocity at its
+ * previous check, -1 if there was none (or no step since, or u = 0), NaN if
+ * it holds non-finite values; inactive lattices keep their last value.
+ * Returns LBM_ERR_UNSTABLE when a lattice holds non-finite values and
+ * LBM_ERR_TIMEOUT when a step kernel gave up a bounded wait. */
+lbm_status lbm_batch_residuals(lbm_batch* b, double* res);
+
+/* Run to a steady state: check the residuals, then repeat {step
+ * check_every (>= 1) steps; check} until every lattice is inactive or
+ * max_steps steps have been taken in this call.  A lattice whose residual
+ * is in [0, tol] is retired at that check; one that holds non-finite values
+ * is retired too and the call returns LBM_ERR_UNSTABLE after the others
+ * finish.  Lattices still active at max_steps stay active.  res: nullable,
+ * count doubles, the last residual of each lattice. */
+lbm_status lbm_batch_run(lbm_batch* b, double tol, int64_t check_every,
+                         int64_t max_steps, double* res);
+
+/* Retire (on = 0) or re-activate (on = 1) lattice k. */
+lbm_status lbm_batch_set_active(lbm_batch* b, int k, int on);
+
+/* 1 if lattice k is active, 0 if retired, -1 for a bad argument. */
+int lbm_batch_is_active(const lbm_batch* b, int k);
+
+/* Launch shape of the batch step: threads per block along x (32, 64 or 128;
+ * a block covers 2 x block_x columns) and target rows per band (1 .. 65536;
+ * lattice k gets max(1, round(ny_k / rows_per_band)) bands).  The shape
+ * changes the schedule only, never the results.  Default 32, 16. */
+lbm_status lbm_batch_set_shape(lbm_batch* b, int block_x, int rows_per_band);
+lbm_status lbm_batch_get_shape(const lbm_batch* b, int* block_x, int* rows_per_band);
+
+/* Autotuner: times trial_steps (>= 1) steps of the active lattices at each
+ * block_x in {32, 64, 128} and rows_per_band in {8, 16, 32, 64} (one warm-up
+ * step each, CUDA events on the batch's stream), keeps the fastest shape and
+ * returns it (outputs nullable).  The trial steps are real steps of the
+ * active lattices (12 (trial_steps + 1) in all): the shape does not change
+ * the results.  Synchronous. */
+lbm_status lbm_batch_tune(lbm_batch* b, int trial_steps, int* block_x,
+                          int* rows_per_band);
+
+/* lbm_moments, lbm_get_f and lbm_diagnostics for lattice k.  The
+ * diagnostics' out[4] is the lattice's last residual of
+ * lbm_batch_residuals / lbm_batch_run. */
+lbm_status lbm_batch_moments(lbm_batch* b, int k, double* rho, double* ux,
+                             double* uy, int on_device);
+lbm_status lbm_batch_get_f(lbm_batch* b, int k, double* f, int on_device);
+lbm_status lbm_batch_diagnostics(lbm_batch* b, int k, double out[LBM_DIAG_COUNT]);
+
+/* Steps taken by lattice k since its last init (-1 for a bad argument). */
+int64_t lbm_batch_step_count(const lbm_batch* b, int k);
+
+/* Batch step kernel launches issued so far (one per step). */
+int64_t lbm_batch_launch_count(const lbm_batch* b);
+
+/* Message of the last error on b (or of the last failed lbm_batch_create
+ * when b is NULL); never NULL. */
+const char* lbm_batch_last_error(const lbm_batch* b);
 
 #ifdef __cplusplus
 }

@@ -632,6 +632,46 @@ int orc_strain(const orc* o, double* dxux, double* dyuy)
     return 0;
 }
 
+int orc_stress(const orc* o, double* sxy, double* txx, double* tyy,
+               double* txy)
+{
+    if (!o) return -1;
+    orc* w = (orc*)o; /* refreshes the rho / gradient scratch only */
+    density(w);
+    density_gradient(w);
+    const int N = o->N;
+    const double cs2 = o->p.cs2;
+    const double* om = o->p.omega;
+    /* Eq. 32-33: shear viscosity from omega_4 (normal) and omega_5 (shear),
+     * bulk viscosity from omega_3. */
+    const double nu4 = cs2 * (1.0 / om[4] - 0.5);
+    const double nu5 = cs2 * (1.0 / om[5] - 0.5);
+    const double zeta = cs2 * (1.0 / om[3] - 0.5);
+#pragma omp parallel for num_threads(nthreads_of(o)) schedule(static)
+    for (int c = 0; c < N; ++c) {
+        double f[9], ft[9], m[9], st[2] = {0.0, 0.0};
+        double shear = 0.0, rho = 0.0;
+        if (!o->solid[c]) {
+            for (int i = 0; i < 9; ++i) f[i] = o->f[(size_t)i * N + c];
+            collide(&o->p, o->T, o->Ti, f, o->dxr[c], o->dyr[c], ft, st);
+            matvec9(o->T, f, m);
+            rho = m[0];
+            const double ux = (m[1] + 0.5 * o->p.Fx) / rho;
+            const double uy = (m[2] + 0.5 * o->p.Fy) / rho;
+            /* Eq. 39 with Eq. 36 and D1 of Eq. 40 (left side read as
+             * d_y u_x + d_x u_y, as Eq. 21 gives it). */
+            const double D1 = -rho * cs2 / om[5];
+            shear = (m[5] - rho * ux * uy) / D1;
+        }
+        const double div = st[0] + st[1];
+        if (sxy) sxy[c] = shear;
+        if (txx) txx[c] = rho * (nu4 * (2.0 * st[0] - div) + zeta * div);
+        if (tyy) tyy[c] = rho * (nu4 * (2.0 * st[1] - div) + zeta * div);
+        if (txy) txy[c] = rho * nu5 * shear;
+    }
+    return 0;
+}
+
 int orc_solid(const orc* o, unsigned char* solid)
 {
     if (!o || !solid) return -1;

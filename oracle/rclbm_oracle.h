@@ -83,6 +83,16 @@ int orc_step(orc* o, long n);
 int orc_moments(const orc* o, double* rho, double* ux, double* uy);
 /* Local strain rates (Eq. 37-38) the next collision would use; solid -> 0. */
 int orc_strain(const orc* o, double* dxux, double* dyuy);
+/* Off-diagonal strain rate d_y u_x + d_x u_y of Eq. 39 (its left side read
+ * as the off-diagonal rate, as Eq. 21 gives it) and the viscous stress of the
+ * Navier-Stokes equations the scheme recovers (Eq. 30-33):
+ *   txx = rho [nu (2 d_x u_x - div u) + zeta div u], tyy likewise,
+ *   txy = rho nu (d_y u_x + d_x u_y),
+ * nu = cs2 (1/omega_4 - 1/2) for the normal and cs2 (1/omega_5 - 1/2) for
+ * the shear stress, zeta = cs2 (1/omega_3 - 1/2), with the local rates of
+ * Eq. 37-39 the next collision would use.  Nullable outputs; solid -> 0. */
+int orc_stress(const orc* o, double* sxy, double* txx, double* tyy,
+               double* txy);
 /* The solid map in use (after the isolated-cell rule), N bytes. */
 int orc_solid(const orc* o, unsigned char* solid);
 int orc_threads(const orc* o);

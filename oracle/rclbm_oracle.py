@@ -98,6 +98,7 @@ def lib():
             L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
             L.orc_moments.argtypes = [ctypes.c_void_p, _D, _D, _D]
             L.orc_strain.argtypes = [ctypes.c_void_p, _D, _D]
+            L.orc_stress.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
             L.orc_solid.argtypes = [ctypes.c_void_p, _U8]
             L.orc_threads.argtypes = [ctypes.c_void_p]
             _lib = L
@@ -215,6 +216,12 @@ class Oracle:
         dx, dy = np.zeros((self.ny, self.nx)), np.zeros((self.ny, self.nx))
         lib().orc_strain(self.h, _dp(dx), _dp(dy))
         return dx, dy
+
+    def stress(self):
+        """(d_y u_x + d_x u_y, tau_xx, tau_yy, tau_xy), each (ny, nx)."""
+        out = [np.zeros((self.ny, self.nx)) for _ in range(4)]
+        lib().orc_stress(self.h, *(_dp(x) for x in out))
+        return tuple(out)
 
     def solid(self):
         s = np.zeros((self.ny, self.nx), dtype=np.uint8)

@@ -116,7 +116,8 @@ const char* validate(const lbm_params* p) {
         p->block_x != 256)
         return "block_x must be 0, 32, 64, 128 or 256";
     if (p->bands < 0) return "bands must be >= 0";
-    if (p->scheme != 0 && p->scheme != -1) return "scheme must be 0 (RC-LBM) or -1 (no collision)";
+    if (p->scheme != 0 && p->scheme != 1 && p->scheme != -1)
+        return "scheme must be 0 (RC-LBM), 1 (RNR-LBM) or -1 (no collision)";
     // the 2x2 strain-rate system of Eq. 37-38 must be solvable at rest
     const double cs2 = p->cs2, a2 = p->a * p->a;
     const double b1 = -2 * cs2 / p->omega[3] - (1 - 3 * cs2) / 2;
@@ -127,15 +128,23 @@ const char* validate(const lbm_params* p) {
     return nullptr;
 }
 
+// Storage geometry of one lattice.
+struct Geometry {
+    int pitch;
+    long long plane;
+    int rstride;
+    const uint8_t* lmask;
+    int* status;
+};
+
 template <typename T>
-KParams<T> kparams(const lbm_handle* h) {
-    const lbm_params& q = h->p;
+KParams<T> kparams_of(const lbm_params& q, const Geometry& g) {
     KParams<T> k{};
     k.nx = q.nx;
     k.ny = q.ny;
-    k.pitch = h->pitch;
-    k.plane = h->plane;
-    k.rstride = h->rstride;
+    k.pitch = g.pitch;
+    k.plane = g.plane;
+    k.rstride = g.rstride;
     k.px = q.periodic_x;
     k.py = q.periodic_y;
     k.moving = 0;
@@ -163,6 +172,10 @@ KParams<T> kparams(const lbm_handle* h) {
     k.w8 = T(w[8]);
     k.lw3 = T(1.0 - 0.5 * w[3]);
     k.lw4 = T(1.0 - 0.5 * w[4]);
+    k.lw5 = T(1.0 - 0.5 * w[5]);
+    k.lw6 = T(1.0 - 0.5 * w[6]);
+    k.lw7 = T(1.0 - 0.5 * w[7]);
+    k.lw8 = T(1.0 - 0.5 * w[8]);
     const double g1 = 1.0 - 3.0 * cs2, g2 = a2 - 3.0 * cs2;
     k.g1i = T(q.use_iso_corr ? g1 : 0.0);
     k.g2i = T(q.use_iso_corr ? g2 : 0.0);
@@ -177,32 +190,43 @@ KParams<T> kparams(const lbm_handle* h) {
     k.Fy = T(q.Fy);
     k.hFx = T(0.5 * q.Fx);
     k.hFy = T(0.5 * q.Fy);
-    k.lmask = h->lmask;
-    k.collide = q.scheme == 0;
-    k.status = h->status;
+    k.lmask = g.lmask;
+    k.collide = q.scheme >= 0;
+    k.raw = q.scheme == 1;
+    k.status = g.status;
     return k;
 }
 
-AuxParams aux(const lbm_handle* h) {
+AuxParams aux_of(const lbm_params& q, const Geometry& g) {
     AuxParams a{};
-    a.nx = h->p.nx;
-    a.ny = h->p.ny;
-    a.pitch = h->pitch;
-    a.plane = h->plane;
-    a.rstride = h->rstride;
-    a.px = h->p.periodic_x;
-    a.py = h->p.periodic_y;
-    a.a = h->p.a;
-    a.cs2 = h->p.cs2;
-    a.rho0 = h->p.rho0;
-    a.Fx = h->p.Fx;
-    a.Fy = h->p.Fy;
+    a.nx = q.nx;
+    a.ny = q.ny;
+    a.pitch = g.pitch;
+    a.plane = g.plane;
+    a.rstride = g.rstride;
+    a.px = q.periodic_x;
+    a.py = q.periodic_y;
+    a.a = q.a;
+    a.cs2 = q.cs2;
+    a.rho0 = q.rho0;
+    a.Fx = q.Fx;
+    a.Fy = q.Fy;
     double w[9];
-    rest_weights(h->p.a, h->p.cs2, w);
-    for (int i = 0; i < 9; ++i) a.wrest[i] = w[i] * h->p.rho0;
-    a.lmask = h->lmask;
+    rest_weights(q.a, q.cs2, w);
+    for (int i = 0; i < 9; ++i) a.wrest[i] = w[i] * q.rho0;
+    a.w3 = q.omega[3];
+    a.w4 = q.omega[4];
+    a.w5 = q.omega[5];
+    a.lmask = g.lmask;
     return a;
 }
+
+Geometry geometry(const lbm_handle* h) {
+    return Geometry{h->pitch, h->plane, h->rstride, h->lmask, h->status};
+}
+template <typename T>
+KParams<T> kparams(const lbm_handle* h) { return kparams_of<T>(h->p, geometry(h)); }
+AuxParams aux(const lbm_handle* h) { return aux_of(h->p, geometry(h)); }
 
 // Link mask of every cell (see lbm_device.cuh: bit i-1 = source of
 // direction i is a wall or solid node, 0xFF = solid cell).  Fluid cells
@@ -485,6 +509,45 @@ lbm_status lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, int o
     return LBM_OK;
 }
 
+lbm_status lbm_stress(lbm_handle* h, double* dxux, double* dyuy, double* sxy, double* txx,
+                      double* tyy, double* txy, int on_device) {
+    if (!h) return LBM_ERR_INVALID;
+    const size_t N = (size_t)h->N;
+    double* outs[6] = {dxux, dyuy, sxy, txx, tyy, txy};
+    double* d[6];
+    // staging: the density field, then (host outputs) one slot per output
+    lbm_status s = ensure_stage(h, on_device ? N : 7 * N);
+    if (s != LBM_OK) return s;
+    double* rho = h->stage;
+    for (int i = 0; i < 6; ++i)
+        d[i] = (on_device || !outs[i]) ? outs[i] : h->stage + N * (i + 1);
+    const AuxParams a = aux(h);
+    cudaError_t e;
+    if (h->p.precision == 64) {
+        e = lbm::launch_moments<double>((const double*)h->f[h->cur], a, rho, nullptr, nullptr,
+                                        h->stream);
+        if (e == cudaSuccess)
+            e = lbm::launch_stress<double>((const double*)h->f[h->cur], a, rho, d[0], d[1], d[2],
+                                           d[3], d[4], d[5], h->stream);
+    } else {
+        e = lbm::launch_moments<float>((const float*)h->f[h->cur], a, rho, nullptr, nullptr,
+                                       h->stream);
+        if (e == cudaSuccess)
+            e = lbm::launch_stress<float>((const float*)h->f[h->cur], a, rho, d[0], d[1], d[2],
+                                          d[3], d[4], d[5], h->stream);
+    }
+    CK(h, e, "stress kernels");
+    if (!on_device) {
+        for (int i = 0; i < 6; ++i)
+            if (outs[i])
+                CK(h, cudaMemcpyAsync(outs[i], d[i], N * sizeof(double), cudaMemcpyDeviceToHost,
+                                      h->stream),
+                   "cudaMemcpyAsync(D2H)");
+        CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_get_f(lbm_handle* h, double* f, int on_device) {
     if (!h || !f) return LBM_ERR_INVALID;
     const size_t n = 9 * (size_t)h->N;
@@ -741,3 +804,652 @@ extern "C" lbm_status lbm_diagnostics_noalloc(lbm_handle* h, double out[LBM_DIAG
     }
     return LBM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batches: many independent FP32 lattices of uneven size advanced together.
+//
+// Every step of a batch is one launch of the persistent batch kernel over a
+// device work list of (lattice, column segment, band of rows) items of the
+// active lattices; the lattice table (parameters, link mask, buffers) lives
+// in device memory.  Runs of kGraphSteps steps are replayed from a CUDA
+// graph captured once per (launch shape, start parity).  Residual checks
+// reduce every active lattice in two launches; lattices whose residual
+// reaches the tolerance are retired from the work list.
+// ---------------------------------------------------------------------------
+using lbm::BatchAux;
+using lbm::BatchLattice;
+using lbm::ResPartial;
+
+namespace {
+constexpr int kGraphSteps = 50;        // steps per captured graph (even)
+constexpr int kResCellsPerBlock = 2048;  // cells per residual reduction block
+}  // namespace
+
+struct lbm_batch {
+    int count = 0;
+    cudaStream_t stream = nullptr;  // borrowed
+    cudaStream_t cap = nullptr;     // owned, for graph capture only
+    int sms = 1;
+    std::vector<lbm_params> p;
+    std::vector<Geometry> geo;
+    std::vector<long long> N, n_fluid;
+    std::vector<BatchLattice<float>> lat;  // host copy of the table
+    std::vector<BatchAux> bax;
+    std::vector<int> cur;                  // index into lat[k].f of the state
+    std::vector<char> active, have_prev, unstable;
+    std::vector<int64_t> steps, prev_step;
+    std::vector<double> last_res;
+    float* fbase = nullptr;
+    uint8_t* mbase = nullptr;
+    double* ubase = nullptr;
+    BatchLattice<float>* d_lat = nullptr;
+    BatchAux* d_aux = nullptr;
+    int* d_list = nullptr;  // active[count] begin[count] rbegin[count] counts[2] rcounts[2]
+    std::vector<int> h_list;
+    int n_active = 0, total_items = 0, total_chunks = 0;
+    bool list_dirty = true;
+    ResPartial* d_part = nullptr;  // per reduction block
+    ResPartial* d_res = nullptr;   // per lattice
+    std::vector<ResPartial> h_res;
+    DiagPartial* d_diag = nullptr; // lbm_batch_diagnostics
+    int diag_blocks = 0;
+    int* status = nullptr;
+    double* stage = nullptr;
+    size_t stage_elems = 0;
+    int parity = 0;
+    int bx = 32, rows = 16, grid = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t launches = 0;
+    char err[512] = {0};
+};
+
+namespace {
+
+void bset_err(lbm_batch* b, const char* fmt, ...) {
+    char* dst = b ? b->err : g_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+}
+
+lbm_status bcuda_fail(lbm_batch* b, cudaError_t e, const char* what) {
+    bset_err(b, "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+#define BCK(b, call, what)                                     \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return bcuda_fail(b, e_, what); \
+    } while (0)
+
+void drop_graphs(lbm_batch* b) {
+    for (auto& g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// Work items of lattice k at the batch's launch shape.
+void shape_lattice(lbm_batch* b, int k) {
+    BatchLattice<float>& L = b->lat[k];
+    const int W = lbm::step_segment_width<float>(b->bx);
+    L.nseg = (b->p[k].nx + W - 1) / W;
+    int nb = (b->p[k].ny + b->rows / 2) / b->rows;
+    if (nb < 1) nb = 1;
+    if (nb > b->p[k].ny) nb = b->p[k].ny;
+    L.nbands = nb;
+}
+
+lbm_status set_shape(lbm_batch* b, int bx, int rows) {
+    if (b->bx == bx && b->rows == rows && b->grid > 0) return LBM_OK;
+    b->bx = bx;
+    b->rows = rows;
+    b->grid = lbm::batch_occupancy<float>(bx) * b->sms;
+    for (int k = 0; k < b->count; ++k) shape_lattice(b, k);
+    BCK(b, cudaMemcpyAsync(b->d_lat, b->lat.data(), sizeof(BatchLattice<float>) * b->count,
+                           cudaMemcpyHostToDevice, b->stream),
+        "cudaMemcpyAsync(lattice table)");
+    drop_graphs(b);
+    b->list_dirty = true;
+    return LBM_OK;
+}
+
+// Uploads the work lists of the active lattices (if they changed).
+lbm_status upload_list(lbm_batch* b) {
+    if (!b->list_dirty) return LBM_OK;
+    const int C = b->count;
+    int n = 0;
+    long long items = 0, chunks = 0;
+    for (int k = 0; k < C; ++k) {
+        if (!b->active[k]) continue;
+        b->h_list[n] = k;
+        b->h_list[C + n] = (int)items;
+        b->h_list[2 * C + n] = (int)chunks;
+        items += (long long)b->lat[k].nseg * b->lat[k].nbands;
+        chunks += b->bax[k].nchunk;
+        ++n;
+    }
+    if (items > (1LL << 30) || chunks > (1LL << 30)) {
+        bset_err(b, "the batch's work list is too long");
+        return LBM_ERR_INVALID;
+    }
+    b->h_list[3 * C] = n;
+    b->h_list[3 * C + 1] = (int)items;
+    b->h_list[3 * C + 2] = n;
+    b->h_list[3 * C + 3] = (int)chunks;
+    BCK(b, cudaMemcpyAsync(b->d_list, b->h_list.data(), sizeof(int) * (3 * C + 4),
+                           cudaMemcpyHostToDevice, b->stream),
+        "cudaMemcpyAsync(work list)");
+    b->n_active = n;
+    b->total_items = (int)items;
+    b->total_chunks = (int)chunks;
+    b->list_dirty = false;
+    return LBM_OK;
+}
+
+cudaError_t launch_steps(lbm_batch* b, int n, int parity, cudaStream_t s) {
+    const int C = b->count;
+    for (int i = 0; i < n; ++i) {
+        cudaError_t e = lbm::launch_batch_step<float>(b->d_lat, b->d_list, b->d_list + C,
+                                                      b->d_list + 3 * C, (parity + i) & 1,
+                                                      b->bx, b->grid, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+lbm_status ensure_graph(lbm_batch* b, int parity) {
+    if (b->graph[parity]) return LBM_OK;
+    BCK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+    cudaError_t e = launch_steps(b, kGraphSteps, parity, b->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bcuda_fail(b, e != cudaSuccess ? e : e2, "graph capture of the batch step");
+    }
+    e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    BCK(b, e, "cudaGraphInstantiate");
+    return LBM_OK;
+}
+
+// A handle that views lattice k of a batch, for the single-lattice read-out
+// and set-up entry points.  It owns nothing; release_view hands the staging
+// buffer (which those entry points may grow) back to the batch.
+void make_view(lbm_batch* b, int k, lbm_handle& h) {
+    h.p = b->p[k];
+    h.pitch = b->geo[k].pitch;
+    h.plane = b->geo[k].plane;
+    h.rstride = b->geo[k].rstride;
+    h.N = b->N[k];
+    h.n_fluid = b->n_fluid[k];
+    h.stream = b->stream;
+    h.f[0] = b->lat[k].f[b->cur[k]];
+    h.f[1] = nullptr;
+    h.cur = 0;
+    h.lmask = const_cast<uint8_t*>(b->geo[k].lmask);
+    h.stage = b->stage;
+    h.stage_elems = b->stage_elems;
+    h.part = b->d_diag;
+    h.diag_blocks = b->diag_blocks;
+    h.status = b->status;
+    h.steps = b->steps[k];
+}
+
+lbm_status release_view(lbm_batch* b, lbm_handle& h, lbm_status s) {
+    b->stage = h.stage;
+    b->stage_elems = h.stage_elems;
+    if (s != LBM_OK) std::snprintf(b->err, sizeof(b->err), "%s", h.err);
+    return s;
+}
+
+bool bad_index(lbm_batch* b, int k) {
+    if (!b) return true;
+    if (k < 0 || k >= b->count) {
+        bset_err(b, "lattice index %d outside [0, %d)", k, b->count);
+        return true;
+    }
+    return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(const lbm_params* params, int count,
+                            const uint8_t* const* solid_masks, void* cuda_stream,
+                            lbm_batch** out) {
+    if (!out) {
+        set_err(nullptr, "out is NULL");
+        return LBM_ERR_INVALID;
+    }
+    *out = nullptr;
+    if (!params || count < 1 || count > (1 << 20)) {
+        set_err(nullptr, "a batch needs 1 to 2^20 lattice parameter sets");
+        return LBM_ERR_INVALID;
+    }
+    for (int k = 0; k < count; ++k) {
+        const lbm_params& q = params[k];
+        const char* why = validate(&q);
+        if (!why && q.precision != 32) why = "batches hold FP32 lattices only (precision 32)";
+        if (!why && 9LL * ((q.nx + 31) / 32 * 32) * q.ny >= (1LL << 31))
+            why = "a lattice of a batch must hold fewer than 2^31 values per buffer";
+        if (why) {
+            set_err(nullptr, "invalid parameters of lattice %d: %s", k, why);
+            return LBM_ERR_INVALID;
+        }
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) {
+        set_err(nullptr, "host allocation failed");
+        return LBM_ERR_OOM;
+    }
+    auto fail = [&](lbm_status s) {
+        std::snprintf(g_err, sizeof(g_err), "%s", b->err);
+        lbm_batch_destroy(b);
+        return s;
+    };
+#define BCKC(call, what)                                            \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return fail(bcuda_fail(b, e_, what)); \
+    } while (0)
+    b->count = count;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->p.assign(params, params + count);
+    b->geo.resize(count);
+    b->N.resize(count);
+    b->n_fluid.resize(count);
+    b->lat.resize(count);
+    b->bax.resize(count);
+    b->cur.assign(count, 0);
+    b->active.assign(count, 1);
+    b->have_prev.assign(count, 0);
+    b->unstable.assign(count, 0);
+    b->steps.assign(count, 0);
+    b->prev_step.assign(count, 0);
+    b->last_res.assign(count, -1.0);
+    b->h_list.assign(3 * (size_t)count + 4, 0);
+    b->h_res.resize(count);
+
+    // one allocation each for the populations (two buffers per lattice), the
+    // link masks and the residual reference fields; 256-byte aligned parts
+    auto up = [](size_t v, size_t a) { return (v + a - 1) / a * a; };
+    std::vector<size_t> foff(count), moff(count), uoff(count);
+    size_t fl = 0, ml = 0, ul = 0;
+    long long chunks = 0;
+    for (int k = 0; k < count; ++k) {
+        const lbm_params& q = params[k];
+        Geometry& g = b->geo[k];
+        g.pitch = (q.nx + 31) / 32 * 32;
+        g.plane = (long long)g.pitch * q.ny;
+        g.rstride = g.pitch;
+        b->N[k] = (long long)q.nx * q.ny;
+        foff[k] = fl;
+        fl += 2 * up(9 * (size_t)g.plane, 64);
+        moff[k] = ml;
+        ml += up((size_t)g.plane, 256);
+        uoff[k] = ul;
+        ul += up(2 * (size_t)b->N[k], 32);
+        b->bax[k].nchunk = (int)((b->N[k] + kResCellsPerBlock - 1) / kResCellsPerBlock);
+        b->bax[k].pbegin = (int)chunks;
+        chunks += b->bax[k].nchunk;
+    }
+    if (chunks > (1LL << 30)) {
+        bset_err(b, "the batch is too large");
+        return fail(LBM_ERR_INVALID);
+    }
+    int dev = 0;
+    BCKC(cudaGetDevice(&dev), "cudaGetDevice");
+    BCKC(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev),
+         "cudaDeviceGetAttribute");
+    BCKC(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    BCKC(cudaMalloc(&b->fbase, fl * sizeof(float)), "cudaMalloc(distributions)");
+    BCKC(cudaMalloc(&b->mbase, ml), "cudaMalloc(link masks)");
+    BCKC(cudaMalloc(&b->ubase, ul * sizeof(double)), "cudaMalloc(residual fields)");
+    BCKC(cudaMemsetAsync(b->fbase, 0, fl * sizeof(float), b->stream), "cudaMemset");
+    BCKC(cudaMemsetAsync(b->ubase, 0, ul * sizeof(double), b->stream), "cudaMemset");
+    BCKC(cudaMalloc(&b->status, sizeof(int)), "cudaMalloc(status)");
+    BCKC(cudaMemsetAsync(b->status, 0, sizeof(int), b->stream), "cudaMemset");
+    BCKC(cudaMalloc(&b->d_lat, sizeof(BatchLattice<float>) * count), "cudaMalloc(lattice table)");
+    BCKC(cudaMalloc(&b->d_aux, sizeof(BatchAux) * count), "cudaMalloc(lattice table)");
+    BCKC(cudaMalloc(&b->d_list, sizeof(int) * (3 * (size_t)count + 4)), "cudaMalloc(work list)");
+    BCKC(cudaMalloc(&b->d_part, sizeof(ResPartial) * (size_t)chunks), "cudaMalloc(residual sums)");
+    BCKC(cudaMalloc(&b->d_res, sizeof(ResPartial) * (size_t)count), "cudaMalloc(residual sums)");
+    b->diag_blocks = 2 * b->sms;
+    BCKC(cudaMalloc(&b->d_diag, sizeof(DiagPartial) * (b->diag_blocks + 1)),
+         "cudaMalloc(diagnostics)");
+
+    std::vector<uint8_t> zero, lm;
+    for (int k = 0; k < count; ++k) {
+        const lbm_params& q = params[k];
+        Geometry& g = b->geo[k];
+        const uint8_t* solid = solid_masks ? solid_masks[k] : nullptr;
+        if (!solid) {
+            zero.assign((size_t)b->N[k], 0);
+            solid = zero.data();
+        }
+        b->n_fluid[k] = build_link_mask(q, solid, g.pitch, lm);
+        uint8_t* dm = b->mbase + moff[k];
+        BCKC(cudaMemcpy(dm, lm.data(), lm.size(), cudaMemcpyHostToDevice), "cudaMemcpy(link mask)");
+        g.lmask = dm;
+        g.status = b->status;
+        BatchLattice<float>& L = b->lat[k];
+        L.kp = kparams_of<float>(q, g);
+        L.f[0] = b->fbase + foff[k];
+        L.f[1] = b->fbase + foff[k] + up(9 * (size_t)g.plane, 64);
+        b->bax[k].a = aux_of(q, g);
+        b->bax[k].uprev = b->ubase + uoff[k];
+    }
+    BCKC(cudaMemcpyAsync(b->d_aux, b->bax.data(), sizeof(BatchAux) * count,
+                         cudaMemcpyHostToDevice, b->stream),
+         "cudaMemcpyAsync(lattice table)");
+    b->grid = 0;
+    if (lbm_status s = set_shape(b, 32, 16); s != LBM_OK) return fail(s);
+    for (int k = 0; k < count; ++k)
+        if (lbm_status s = lbm_batch_init_fields(b, k, nullptr, nullptr, nullptr, 1); s != LBM_OK)
+            return fail(s);
+    BCKC(cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+#undef BCKC
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    drop_graphs(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->fbase);
+    cudaFree(b->mbase);
+    cudaFree(b->ubase);
+    cudaFree(b->d_lat);
+    cudaFree(b->d_aux);
+    cudaFree(b->d_list);
+    cudaFree(b->d_part);
+    cudaFree(b->d_res);
+    cudaFree(b->d_diag);
+    cudaFree(b->status);
+    cudaFree(b->stage);
+    delete b;
+}
+
+int lbm_batch_count(const lbm_batch* b) { return b ? b->count : -1; }
+
+lbm_status lbm_batch_init_fields(lbm_batch* b, int k, const double* rho, const double* ux,
+                                 const double* uy, int on_device) {
+    if (bad_index(b, k)) return LBM_ERR_INVALID;
+    lbm_handle h;
+    make_view(b, k, h);
+    lbm_status s = release_view(b, h, lbm_init_fields(&h, rho, ux, uy, on_device));
+    if (s != LBM_OK) return s;
+    b->steps[k] = 0;
+    b->have_prev[k] = 0;
+    b->prev_step[k] = 0;
+    b->unstable[k] = 0;
+    b->last_res[k] = -1.0;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_active(lbm_batch* b, int k, int on) {
+    if (bad_index(b, k)) return LBM_ERR_INVALID;
+    if ((b->active[k] != 0) == (on != 0)) return LBM_OK;
+    if (on && b->cur[k] != b->parity) {
+        // the active lattices step from f[parity]: swap this one's buffers
+        BatchLattice<float>& L = b->lat[k];
+        float* t = L.f[0];
+        L.f[0] = L.f[1];
+        L.f[1] = t;
+        b->cur[k] = b->parity;
+        BCK(b, cudaMemcpyAsync(b->d_lat + k, &L, sizeof(L), cudaMemcpyHostToDevice, b->stream),
+            "cudaMemcpyAsync(lattice table)");
+    }
+    b->active[k] = on != 0;
+    b->list_dirty = true;
+    return LBM_OK;
+}
+
+int lbm_batch_is_active(const lbm_batch* b, int k) {
+    return (b && k >= 0 && k < b->count) ? (int)b->active[k] : -1;
+}
+
+lbm_status lbm_batch_set_shape(lbm_batch* b, int block_x, int rows_per_band) {
+    if (!b) return LBM_ERR_INVALID;
+    if (block_x != 32 && block_x != 64 && block_x != 128) {
+        bset_err(b, "block_x must be 32, 64 or 128");
+        return LBM_ERR_INVALID;
+    }
+    if (rows_per_band < 1 || rows_per_band > 1 << 16) {
+        bset_err(b, "rows_per_band must lie in [1, 65536]");
+        return LBM_ERR_INVALID;
+    }
+    return set_shape(b, block_x, rows_per_band);
+}
+
+lbm_status lbm_batch_get_shape(const lbm_batch* b, int* block_x, int* rows_per_band) {
+    if (!b) return LBM_ERR_INVALID;
+    if (block_x) *block_x = b->bx;
+    if (rows_per_band) *rows_per_band = b->rows;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// nsteps steps of every active lattice; runs of kGraphSteps replay a graph
+// when `graphs` is set, the rest are launched one by one.
+lbm_status advance(lbm_batch* b, int64_t nsteps, bool graphs) {
+    if (lbm_status s = upload_list(b); s != LBM_OK) return s;
+    if (b->n_active == 0 || nsteps == 0) return LBM_OK;
+    int64_t left = nsteps;
+    while (graphs && left >= kGraphSteps) {
+        if (lbm_status s = ensure_graph(b, b->parity); s != LBM_OK) return s;
+        BCK(b, cudaGraphLaunch(b->graph[b->parity], b->stream), "cudaGraphLaunch");
+        left -= kGraphSteps;
+        b->launches += kGraphSteps;
+    }
+    while (left > 0) {
+        const int n = left < (1 << 20) ? (int)left : (1 << 20);
+        BCK(b, launch_steps(b, n, (int)((b->parity + (nsteps - left)) & 1), b->stream),
+            "batch step kernel");
+        b->launches += n;
+        left -= n;
+    }
+    b->parity = (int)((b->parity + nsteps) & 1);
+    for (int k = 0; k < b->count; ++k)
+        if (b->active[k]) {
+            b->steps[k] += nsteps;
+            b->cur[k] = b->parity;
+        }
+    return LBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+    if (!b) return LBM_ERR_INVALID;
+    if (nsteps < 0) {
+        bset_err(b, "nsteps must be >= 0");
+        return LBM_ERR_INVALID;
+    }
+    return advance(b, nsteps, true);
+}
+
+lbm_status lbm_batch_residuals(lbm_batch* b, double* res) {
+    if (!b) return LBM_ERR_INVALID;
+    if (lbm_status s = upload_list(b); s != LBM_OK) return s;
+    const int C = b->count;
+    int kstatus = 0;
+    if (b->n_active > 0) {
+        BCK(b, lbm::launch_batch_residual(b->d_lat, b->d_aux, b->d_list, b->d_list + 2 * C,
+                                          b->d_list + 3 * C + 2, b->parity, b->d_part, b->d_res,
+                                          b->n_active, b->total_chunks, b->stream),
+            "batch residual kernels");
+        BCK(b, cudaMemcpyAsync(b->h_res.data(), b->d_res, sizeof(ResPartial) * C,
+                               cudaMemcpyDeviceToHost, b->stream),
+            "cudaMemcpyAsync(D2H)");
+    }
+    BCK(b, cudaMemcpyAsync(&kstatus, b->status, sizeof(int), cudaMemcpyDeviceToHost, b->stream),
+        "cudaMemcpyAsync(D2H)");
+    BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    if (kstatus) {
+        bset_err(b, "a batch step kernel gave up waiting for its staged data (status %d)", kstatus);
+        return LBM_ERR_TIMEOUT;
+    }
+    int bad = 0;
+    for (int k = 0; k < C; ++k) {
+        if (b->active[k]) {
+            const ResPartial& r = b->h_res[k];
+            double R = -1.0;
+            if (r.nonfinite > 0) {
+                R = NAN;
+                b->unstable[k] = 1;
+            } else if (b->have_prev[k] && b->steps[k] > b->prev_step[k] && r.ures > 0.0) {
+                R = std::sqrt(r.dres) /
+                    ((double)(b->steps[k] - b->prev_step[k]) * std::sqrt(r.ures));
+            }
+            b->last_res[k] = R;
+            b->have_prev[k] = 1;
+            b->prev_step[k] = b->steps[k];
+        }
+        bad += b->unstable[k];
+        if (res) res[k] = b->last_res[k];
+    }
+    if (bad) {
+        bset_err(b, "%d lattices hold non-finite values", bad);
+        return LBM_ERR_UNSTABLE;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_run(lbm_batch* b, double tol, int64_t check_every, int64_t max_steps,
+                         double* res) {
+    if (!b) return LBM_ERR_INVALID;
+    if (!(tol >= 0.0) || check_every < 1 || max_steps < 0) {
+        bset_err(b, "need tol >= 0, check_every >= 1 and max_steps >= 0");
+        return LBM_ERR_INVALID;
+    }
+    // a first check sets the reference velocity of every active lattice
+    lbm_status s = lbm_batch_residuals(b, nullptr);
+    if (s != LBM_OK && s != LBM_ERR_UNSTABLE) return s;
+    bool unstable = s == LBM_ERR_UNSTABLE;
+    for (int k = 0; k < b->count; ++k)
+        if (b->active[k] && b->unstable[k]) lbm_batch_set_active(b, k, 0);
+    int64_t done = 0;
+    while (done < max_steps) {
+        bool any = false;
+        for (int k = 0; k < b->count; ++k) any |= b->active[k] != 0;
+        if (!any) break;
+        const int64_t n = max_steps - done < check_every ? max_steps - done : check_every;
+        if ((s = lbm_batch_step(b, n)) != LBM_OK) return s;
+        done += n;
+        s = lbm_batch_residuals(b, nullptr);
+        if (s != LBM_OK && s != LBM_ERR_UNSTABLE) return s;
+        unstable |= s == LBM_ERR_UNSTABLE;
+        for (int k = 0; k < b->count; ++k) {
+            if (!b->active[k]) continue;
+            const double R = b->last_res[k];
+            if (b->unstable[k] || (R >= 0.0 && R <= tol))
+                if ((s = lbm_batch_set_active(b, k, 0)) != LBM_OK) return s;
+        }
+    }
+    if (res)
+        for (int k = 0; k < b->count; ++k) res[k] = b->last_res[k];
+    if (unstable) {
+        int bad = 0;
+        for (int k = 0; k < b->count; ++k) bad += b->unstable[k];
+        bset_err(b, "%d lattices hold non-finite values (retired)", bad);
+        return LBM_ERR_UNSTABLE;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_tune(lbm_batch* b, int trial_steps, int* block_x, int* rows_per_band) {
+    if (!b) return LBM_ERR_INVALID;
+    if (trial_steps < 1) {
+        bset_err(b, "trial_steps must be >= 1");
+        return LBM_ERR_INVALID;
+    }
+    static const int kBx[] = {32, 64, 128};
+    static const int kRows[] = {8, 16, 32, 64};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BCK(b, cudaEventCreate(&e0), "cudaEventCreate");
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return bcuda_fail(b, ce, "cudaEventCreate");
+    }
+    float best = 0.0f;
+    int bbx = b->bx, brows = b->rows;
+    lbm_status s = LBM_OK;
+    for (int bx : kBx) {
+        for (int rows : kRows) {
+            if ((s = set_shape(b, bx, rows)) != LBM_OK) break;
+            if ((s = advance(b, 1, false)) != LBM_OK) break;  // warm-up
+            if ((ce = cudaEventRecord(e0, b->stream)) != cudaSuccess) break;
+            if ((s = advance(b, trial_steps, false)) != LBM_OK) break;
+            if ((ce = cudaEventRecord(e1, b->stream)) != cudaSuccess) break;
+            if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.0f;
+            if ((ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+            if (best == 0.0f || ms < best) {
+                best = ms;
+                bbx = bx;
+                brows = rows;
+            }
+        }
+        if (s != LBM_OK || ce != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != LBM_OK) return s;
+    if (ce != cudaSuccess) return bcuda_fail(b, ce, "autotuner timing");
+    if ((s = set_shape(b, bbx, brows)) != LBM_OK) return s;
+    if (block_x) *block_x = bbx;
+    if (rows_per_band) *rows_per_band = brows;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_moments(lbm_batch* b, int k, double* rho, double* ux, double* uy,
+                             int on_device) {
+    if (bad_index(b, k)) return LBM_ERR_INVALID;
+    lbm_handle h;
+    make_view(b, k, h);
+    return release_view(b, h, lbm_moments(&h, rho, ux, uy, on_device));
+}
+
+lbm_status lbm_batch_get_f(lbm_batch* b, int k, double* f, int on_device) {
+    if (bad_index(b, k)) return LBM_ERR_INVALID;
+    lbm_handle h;
+    make_view(b, k, h);
+    return release_view(b, h, lbm_get_f(&h, f, on_device));
+}
+
+lbm_status lbm_batch_diagnostics(lbm_batch* b, int k, double out[LBM_DIAG_COUNT]) {
+    if (bad_index(b, k) || !out) return LBM_ERR_INVALID;
+    lbm_handle h;
+    make_view(b, k, h);
+    // the residual of a batch lattice comes from lbm_batch_residuals; here the
+    // staging buffer stands in for the reference velocity field
+    lbm_status s = ensure_stage(&h, 2 * (size_t)h.N);
+    if (s != LBM_OK) return release_view(b, h, s);
+    h.uprev = h.stage;
+    s = lbm_diagnostics(&h, out);
+    h.uprev = nullptr;
+    out[4] = b->last_res[k];
+    return release_view(b, h, s);
+}
+
+int64_t lbm_batch_step_count(const lbm_batch* b, int k) {
+    return (b && k >= 0 && k < b->count) ? b->steps[k] : -1;
+}
+
+int64_t lbm_batch_launch_count(const lbm_batch* b) { return b ? b->launches : -1; }
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : g_err; }
+
+}  // extern "C"

@@ -39,10 +39,12 @@ struct KParams {
     int px, py;               // periodic along x / y
     int moving;               // some wall moves
     int collide;              // 0: streaming and bounce-back only
+    int raw;                  // 1: raw-moment collision (RNR-LBM, Sec. 3)
     T a, iah, ia2, iah2;      // a, 1/(2a), 1/a^2, 1/(2a^2)
     T a2, cs2, cs4, rho0;
     T w3, w4, w5, w6, w7, w8; // relaxation rates
     T lw3, lw4;               // w_j (1/w_j - 1/2) = 1 - w_j/2
+    T lw5, lw6, lw7, lw8;     // 1 - w_j/2 (raw source moments, RNR-LBM)
     T g1i, g2i, g3;           // iso * (1 - 3cs2), iso * (a^2 - 3cs2), gi * 3
     T g1h, g2h;               // (1 - 3cs2)/2, (a^2 - 3cs2)/2 (strain solve)
     T b1c, b2c, c1c, c2c;     // rho-free, u-free parts of B1, B2, C1, C2 (Eq. 40)
@@ -60,6 +62,7 @@ struct AuxParams {
     int px, py;
     double a, cs2, rho0, Fx, Fy;
     double wrest[9];          // rest weights times rho0
+    double w3, w4, w5;        // relaxation rates of the second-order moments
     const uint8_t* __restrict__ lmask;
 };
 
@@ -238,6 +241,113 @@ __device__ __forceinline__ T collide(const KParams<T>& p, T f[9], T d, T dxr, T 
             const T m2 = h[c][2] + uy * (h[c][1] + m1);
             const T t2 = p.iah2 * m2, t1 = p.iah * m1;
             f[iz[c]] += m0 - p.ia2 * m2;
+            f[ip[c]] += t2 + t1;
+            f[im[c]] += t2 - t1;
+        }
+    }
+    return rho;
+}
+
+// Collision of one cell of the raw-moment scheme (RNR-LBM, Sec. 3), in the
+// increment form of collide():
+//   f~ = f + T^-1 [ Lambda (m^eq - m) + (I - Lambda/2) Phi ]
+// with the raw equilibria of Eq. 12 (m^eq_8 = rho cs2^2 + rho cs2 |u|^2 +
+// rho ux^2 uy^2, the binomial transform of the central equilibria), the
+// corrections of Eq. 23-26 on m3 and m4, and the raw source moments of
+// Eq. 13.  The raw moments factor as R[p][q] = sum_i f_i e_ix^p e_iy^q, so
+// the transforms are those of collide() at u = 0.  The strain rates
+// (Eq. 37-38) and corrections are the same as in collide().
+template <typename T>
+__device__ __forceinline__ T collide_raw(const KParams<T>& p, T f[9], T d, T dxr, T dyr) {
+    const T rho = p.rho0 + d;
+    const T jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
+    const T jy = p.a * ((f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]));
+    const T ir = rcp(rho);
+    const T ux = (jx + p.hFx) * ir;
+    const T uy = (jy + p.hFy) * ir;
+    const T a = p.a, a2 = p.a2, cs2 = p.cs2;
+
+    // Raw moments along y of each column: k0 = sum g, k1 = sum g e_y,
+    // k2 = sum g e_y^2; then along x: R[p][q] = sum_X e_x^p k_q(X).
+    T k0[3], k1[3], k2[3];
+    {
+        const T gz[3] = {f[0], f[1], f[3]}, gp[3] = {f[2], f[5], f[6]},
+                gm[3] = {f[4], f[8], f[7]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T sum = gp[c] + gm[c];
+            k0[c] = gz[c] + sum;
+            k1[c] = a * (gp[c] - gm[c]);
+            k2[c] = a2 * sum;
+        }
+    }
+    T R[3][3];
+    {
+        const T* kq[3] = {k0, k1, k2};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const T S = kq[q][1] + kq[q][2];
+            R[0][q] = kq[q][0] + S;
+            R[1][q] = kq[q][1] - kq[q][2];
+            R[2][q] = S;
+        }
+    }
+    // Non-equilibrium raw moments m - m^{eq,r} (Eq. 12); the stored values
+    // are deviations from rho0 w, whose raw moments are rho0 cs2 on xx and
+    // yy and rho0 cs2^2 on xxyy.
+    const T ux2 = ux * ux, uy2 = uy * uy;
+    const T n20 = R[2][0] - d * cs2 - rho * ux2;
+    const T n02 = R[0][2] - d * cs2 - rho * uy2;
+    const T n11 = R[1][1] - rho * ux * uy;
+    const T n21 = R[2][1] - rho * uy * (cs2 + ux2);
+    const T n12 = R[1][2] - rho * ux * (cs2 + uy2);
+    const T n22 = R[2][2] - d * p.cs4 - rho * (cs2 * (ux2 + uy2) + ux2 * uy2);
+    const T N3 = n20 + n02, N4 = n20 - n02;
+
+    // Local strain rates, Eq. 37-38, and corrections, Eq. 23-26.
+    const T b1 = p.b1c + T(1.5) * ux2, b2 = p.b2c + T(1.5) * uy2;
+    const T c1 = p.c1c + T(1.5) * ux2, c2 = p.c2c - T(1.5) * uy2;
+    const T gx = p.g1h * ux * dxr, gy = p.g2h * uy * dyr;
+    const T R3 = N3 + gx + gy;
+    const T R4 = N4 + gx - gy;
+    const T idet = rcp(rho * (b1 * c2 - b2 * c1));
+    const T dxux = (c2 * R3 - b2 * R4) * idet;
+    const T dyuy = (b1 * R4 - c1 * R3) * idet;
+    const T Px = p.g1i * (rho * dxux + ux * dxr) - p.g3 * rho * ux2 * dxux;
+    const T Py = p.g2i * (rho * dyuy + uy * dyr) - p.g3 * rho * uy2 * dyuy;
+
+    // Relaxation with the raw source moments of Eq. 13: increments of the
+    // raw moments.  m1 relaxes to rho ux = m1 + Fx/2, so its increment is Fx
+    // whatever omega_1 (same for m2).
+    const T Fx = p.Fx, Fy = p.Fy;
+    const T dm3 = p.lw3 * (Px + Py + T(2) * (Fx * ux + Fy * uy)) - p.w3 * N3;
+    const T dm4 = p.lw4 * (Px - Py + T(2) * (Fx * ux - Fy * uy)) - p.w4 * N4;
+    const T D20 = T(0.5) * (dm3 + dm4), D02 = T(0.5) * (dm3 - dm4);
+    const T D11 = p.lw5 * (Fx * uy + Fy * ux) - p.w5 * n11;
+    const T D21 = p.lw6 * (Fy * ux2 + T(2) * Fx * ux * uy) - p.w6 * n21;
+    const T D12 = p.lw7 * (Fx * uy2 + T(2) * Fy * ux * uy) - p.w7 * n12;
+    const T D22 = p.lw8 * T(2) * (Fx * ux * uy2 + Fy * uy * ux2) - p.w8 * n22;
+
+    // Back along x (raw x-moments -> columns), then along y.
+    T h[3][3];
+    {
+        const T Dq0[3] = {T(0), Fx, D20};
+        const T Dq1[3] = {Fy, D11, D21};
+        const T Dq2[3] = {D02, D12, D22};
+        const T* Dq[3] = {Dq0, Dq1, Dq2};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            h[0][q] = Dq[q][0] - Dq[q][2];
+            h[1][q] = T(0.5) * (Dq[q][2] + Dq[q][1]);
+            h[2][q] = T(0.5) * (Dq[q][2] - Dq[q][1]);
+        }
+    }
+    {
+        const int iz[3] = {0, 1, 3}, ip[3] = {2, 5, 6}, im[3] = {4, 8, 7};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T t2 = p.iah2 * h[c][2], t1 = p.iah * h[c][1];
+            f[iz[c]] += h[c][0] - p.ia2 * h[c][2];
             f[ip[c]] += t2 + t1;
             f[im[c]] += t2 - t1;
         }

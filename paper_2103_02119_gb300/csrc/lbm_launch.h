@@ -26,6 +26,43 @@ int step_occupancy(int bx, bool mask);
 template <typename T>
 int step_segment_width(int bx);
 
+// One lattice of a batch, as the persistent batch kernel sees it.
+template <typename T>
+struct BatchLattice {
+    KParams<T> kp;        // its parameters (kp.lmask always set)
+    T* f[2];              // its two population buffers
+    int nseg, nbands;     // its work items: nseg * nbands blocks
+};
+// One step of every active lattice of a batch: counts = {number of active
+// lattices, total work items}, begin[k] = first work item of active[k].
+template <typename T>
+cudaError_t launch_batch_step(const BatchLattice<T>* lat, const int* active, const int* begin,
+                              const int* counts, int parity, int bx, int grid, cudaStream_t s);
+template <typename T>
+int batch_occupancy(int bx);
+
+// One lattice of a batch, as the batch residual kernels see it.
+struct BatchAux {
+    AuxParams a;      // a.lmask always set
+    double* uprev;    // 2 * nx * ny doubles: the velocity at the last check
+    int nchunk;       // reduction blocks of this lattice
+    int pbegin;       // index of its first partial sum
+};
+// Sums of the steady-state residual of one lattice: sum |u - uprev|^2,
+// sum |u|^2 over its fluid cells, and the number of non-finite cells.
+struct ResPartial {
+    double dres, ures;
+    long long nonfinite;
+};
+// Residual sums of every active lattice from its FP32 state lat[k].f[parity]:
+// counts = {active lattices, total reduction blocks}, rbegin[j] = first
+// block of active[j]; writes out[active[j]] and overwrites uprev.  The host
+// passes the same two counts as nactive / nblocks (launch sizes).
+cudaError_t launch_batch_residual(const BatchLattice<float>* lat, const BatchAux* aux,
+                                  const int* active, const int* rbegin, const int* counts,
+                                  int parity, ResPartial* part, ResPartial* out, int nactive,
+                                  int nblocks, cudaStream_t s);
+
 // f = f^eq(rho, u) (device inputs, nullable), written in pull-scheme form.
 template <typename T>
 cudaError_t launch_init(T* f, const AuxParams& p, const double* rho, const double* ux,
@@ -39,6 +76,13 @@ cudaError_t launch_get_f(const T* f, const AuxParams& p, double* fout, cudaStrea
 template <typename T>
 cudaError_t launch_moments(const T* f, const AuxParams& p, double* rho, double* ux,
                            double* uy, cudaStream_t s);
+// Local strain rates and viscous stress (FP64, nullable outputs of nx*ny
+// doubles) of the state; rho: the density field of the same state (from
+// launch_moments).
+template <typename T>
+cudaError_t launch_stress(const T* f, const AuxParams& p, const double* rho, double* dxux,
+                          double* dyuy, double* sxy, double* txx, double* tyy, double* txy,
+                          cudaStream_t s);
 // diagnostics: per-block partials into `part` (nblocks entries) then a final
 // reduction into part[nblocks]; uprev (2*nx*ny doubles) is read (if
 // have_prev) and overwritten with the current velocity.

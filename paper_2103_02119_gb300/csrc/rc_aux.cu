@@ -136,6 +136,74 @@ __global__ void moments_kernel(const T* __restrict__ f, const AuxParams p,
     }
 }
 
+// Local strain rates of one fluid cell from its raw non-equilibrium moments
+// (Eq. 34-40; the left side of Eq. 39 read as d_y u_x + d_x u_y) and the
+// viscous stress of the recovered Navier-Stokes equations (Eq. 30-33), all in
+// FP64.  The density gradient is the central difference of the step (spacing
+// 2 along x and 2a along y), a wall or solid neighbour counting with the
+// cell's own density.
+template <typename T, bool MASK>
+__global__ void stress_kernel(const T* __restrict__ f, const AuxParams p,
+                              const double* __restrict__ rho, double* dxux, double* dyuy,
+                              double* sxy, double* txx, double* tyy, double* txy) {
+    const long long N = (long long)p.nx * p.ny;
+    const double a = p.a, a2 = a * a, cs2 = p.cs2;
+    const double nu4 = cs2 * (1.0 / p.w4 - 0.5), nu5 = cs2 * (1.0 / p.w5 - 0.5);
+    const double zeta = cs2 * (1.0 / p.w3 - 0.5);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % p.nx), y = (int)(c / p.nx);
+        const unsigned sb = link_bits<MASK>(p, x, y);
+        double e_xx = 0.0, e_yy = 0.0, e_xy = 0.0, r = 0.0;
+        if (sb != 0xFFu) {
+            T g[9];
+            pull(f, p, x, y, sb, g);
+            double m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0, m5 = 0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const double fi = (double)g[i] + p.wrest[i];
+                const double ex_ = ex(i), ey_ = a * ey(i);
+                m0 += fi;
+                m1 += fi * ex_;
+                m2 += fi * ey_;
+                m3 += fi * (ex_ * ex_ + ey_ * ey_);
+                m4 += fi * (ex_ * ex_ - ey_ * ey_);
+                m5 += fi * ex_ * ey_;
+            }
+            r = m0;
+            const double ux = (m1 + 0.5 * p.Fx) / r, uy = (m2 + 0.5 * p.Fy) / r;
+            const double rc = rho[c];
+            const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
+            const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
+            const long long row = (long long)y * p.nx;
+            const double rW = (sb & 1u) ? rc : rho[row + xm];
+            const double rS = (sb & 2u) ? rc : rho[(long long)ym * p.nx + x];
+            const double rE = (sb & 4u) ? rc : rho[row + xp];
+            const double rN = (sb & 8u) ? rc : rho[(long long)yp * p.nx + x];
+            const double dxr = 0.5 * (rE - rW), dyr = (rN - rS) / (2.0 * a);
+            const double ux2 = ux * ux, uy2 = uy * uy;
+            const double B1 = r * (-2.0 * cs2 / p.w3 - 0.5 * (1.0 - 3.0 * cs2) + 1.5 * ux2);
+            const double B2 = r * (-2.0 * cs2 / p.w3 - 0.5 * (a2 - 3.0 * cs2) + 1.5 * uy2);
+            const double B3 = 0.5 * (3.0 * cs2 - 1.0) * ux, B4 = 0.5 * (3.0 * cs2 - a2) * uy;
+            const double C1 = r * (-2.0 * cs2 / p.w4 - 0.5 * (1.0 - 3.0 * cs2) + 1.5 * ux2);
+            const double C2 = r * (2.0 * cs2 / p.w4 - 0.5 * (3.0 * cs2 - a2) - 1.5 * uy2);
+            const double C3 = B3, C4 = -B4;
+            const double R3 = m3 - (2.0 * r * cs2 + r * (ux2 + uy2)) - B3 * dxr - B4 * dyr;
+            const double R4 = m4 - r * (ux2 - uy2) - C3 * dxr - C4 * dyr;
+            e_xx = (C2 * R3 - B2 * R4) / (C2 * B1 - C1 * B2);
+            e_yy = (C1 * R3 - B1 * R4) / (C1 * B2 - C2 * B1);
+            e_xy = (m5 - r * ux * uy) / (-r * cs2 / p.w5);
+        }
+        const double div = e_xx + e_yy;
+        if (dxux) dxux[c] = e_xx;
+        if (dyuy) dyuy[c] = e_yy;
+        if (sxy) sxy[c] = e_xy;
+        if (txx) txx[c] = r * (nu4 * (2.0 * e_xx - div) + zeta * div);
+        if (tyy) tyy[c] = r * (nu4 * (2.0 * e_yy - div) + zeta * div);
+        if (txy) txy[c] = r * nu5 * e_xy;
+    }
+}
+
 // Adds v exactly (down to 2^-kMassShift) to a fixed-point number held as
 // 24-bit limbs.  Returns false when v is too large for the accumulator.
 __device__ __forceinline__ bool add_fixed(long long limb[kMassLimbs], double v) {
@@ -259,6 +327,89 @@ __global__ void __launch_bounds__(kThreads) diag_final(DiagPartial* part, int n)
     block_reduce(d, part + n);
 }
 
+// Residual sums of one thread summed over the block, in a fixed order.
+__device__ void res_block_reduce(ResPartial& d, ResPartial* out) {
+    __shared__ ResPartial sh[kThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    d.dres = warp_sum(d.dres);
+    d.ures = warp_sum(d.ures);
+    d.nonfinite = warp_sum(d.nonfinite);
+    if (lane == 0) sh[w] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ResPartial s = sh[0];
+        for (int i = 1; i < (int)(blockDim.x / 32); ++i) {
+            s.dres += sh[i].dres;
+            s.ures += sh[i].ures;
+            s.nonfinite += sh[i].nonfinite;
+        }
+        *out = s;
+    }
+}
+
+// Block w sums reduction chunk w - rbegin[j] of active lattice j: cells
+// chunk * kThreads + t + m * nchunk * kThreads.
+__global__ void __launch_bounds__(kThreads)
+batch_res_kernel(const BatchLattice<float>* __restrict__ lat, const BatchAux* __restrict__ aux,
+                 const int* __restrict__ active, const int* __restrict__ rbegin,
+                 const int* __restrict__ counts, int parity, ResPartial* part) {
+    const int n = counts[0];
+    const int w = blockIdx.x;
+    if (w >= counts[1]) return;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rbegin[mid] <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    const int k = active[lo];
+    const BatchAux& B = aux[k];
+    const AuxParams& p = B.a;
+    const float* f = lat[k].f[parity];
+    const int chunk = w - rbegin[lo];
+    const long long N = (long long)p.nx * p.ny;
+    double* __restrict__ up = B.uprev;
+    ResPartial d = {};
+    for (long long c = (long long)chunk * kThreads + threadIdx.x; c < N;
+         c += (long long)B.nchunk * kThreads) {
+        const int x = (int)(c % p.nx), y = (int)(c / p.nx);
+        const unsigned sb = link_bits<true>(p, x, y);
+        if (sb == 0xFFu) continue;
+        float g[9];
+        pull(f, p, x, y, sb, g);
+        double rho, ux, uy;
+        macro(p, g, rho, ux, uy);
+        if (!isfinite(rho) || !isfinite(ux) || !isfinite(uy)) {
+            d.nonfinite += 1;
+            continue;
+        }
+        const double du = ux - up[c], dv = uy - up[N + c];
+        d.dres += du * du + dv * dv;
+        d.ures += ux * ux + uy * uy;
+        up[c] = ux;
+        up[N + c] = uy;
+    }
+    res_block_reduce(d, part + B.pbegin + chunk);
+}
+
+// Block j sums the chunks of active lattice j in chunk order.
+__global__ void __launch_bounds__(kThreads)
+batch_res_final(const BatchAux* __restrict__ aux, const int* __restrict__ active,
+                const int* __restrict__ counts, const ResPartial* __restrict__ part,
+                ResPartial* out) {
+    if ((int)blockIdx.x >= counts[0]) return;
+    const int k = active[blockIdx.x];
+    const BatchAux& B = aux[k];
+    ResPartial d = {};
+    for (int i = threadIdx.x; i < B.nchunk; i += blockDim.x) {
+        const ResPartial& q = part[B.pbegin + i];
+        d.dres += q.dres;
+        d.ures += q.ures;
+        d.nonfinite += q.nonfinite;
+    }
+    res_block_reduce(d, out + k);
+}
+
 int grid_for(long long N) {
     long long b = (N + kThreads - 1) / kThreads;
     return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -301,6 +452,18 @@ cudaError_t launch_moments(const T* f, const AuxParams& p, double* rho, double* 
 }
 
 template <typename T>
+cudaError_t launch_stress(const T* f, const AuxParams& p, const double* rho, double* dxux,
+                          double* dyuy, double* sxy, double* txx, double* tyy, double* txy,
+                          cudaStream_t s) {
+    const int g = grid_for((long long)p.nx * p.ny);
+    if (p.lmask)
+        stress_kernel<T, true><<<g, kThreads, 0, s>>>(f, p, rho, dxux, dyuy, sxy, txx, tyy, txy);
+    else
+        stress_kernel<T, false><<<g, kThreads, 0, s>>>(f, p, rho, dxux, dyuy, sxy, txx, tyy, txy);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_diag(const T* f, const AuxParams& p, double* uprev, int have_prev,
                         DiagPartial* part, int nblocks, cudaStream_t s) {
     if (p.lmask) diag_kernel<T, true><<<nblocks, kThreads, 0, s>>>(f, p, uprev, have_prev, part);
@@ -308,6 +471,18 @@ cudaError_t launch_diag(const T* f, const AuxParams& p, double* uprev, int have_
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     diag_final<<<1, kThreads, 0, s>>>(part, nblocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_residual(const BatchLattice<float>* lat, const BatchAux* aux,
+                                  const int* active, const int* rbegin, const int* counts,
+                                  int parity, ResPartial* part, ResPartial* out, int nactive,
+                                  int nblocks, cudaStream_t s) {
+    if (nactive <= 0 || nblocks <= 0) return cudaSuccess;
+    batch_res_kernel<<<nblocks, kThreads, 0, s>>>(lat, aux, active, rbegin, counts, parity, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_res_final<<<nactive, kThreads, 0, s>>>(aux, active, counts, part, out);
     return cudaGetLastError();
 }
 
@@ -320,6 +495,9 @@ cudaError_t launch_diag(const T* f, const AuxParams& p, double* uprev, int have_
                                          cudaStream_t);                               \
     template cudaError_t launch_moments<T>(const T*, const AuxParams&, double*,       \
                                            double*, double*, cudaStream_t);           \
+    template cudaError_t launch_stress<T>(const T*, const AuxParams&, const double*,  \
+                                          double*, double*, double*, double*, double*, \
+                                          double*, cudaStream_t);                     \
     template cudaError_t launch_diag<T>(const T*, const AuxParams&, double*, int,     \
                                         DiagPartial*, int, cudaStream_t);
 LBM_AUX_INST(float)

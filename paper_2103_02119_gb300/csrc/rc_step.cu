@@ -131,28 +131,35 @@ constexpr size_t step_smem_bytes() {
 }
 
 // I: element-offset type, int while 9 * plane < 2^31, else long long.
-template <typename T, bool MASK, int BXT, typename I>
-__global__ void __launch_bounds__(BXT)
-rc_step_kernel(const T* __restrict__ fin, T* __restrict__ fout, const KParams<T> p,
-               int nbands) {
+__device__ __forceinline__ void mbar_inval(unsigned bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// One block's work: segment `seg` of columns and row band `band` (of nbands)
+// of one lattice, from fin to fout.  smem: step_smem_bytes<T, BXT>() bytes.
+// Returns false when a wait ran out (the block must stop).
+// PT: KParams<T> (by value: a kernel parameter, read from the constant bank)
+// or const KParams<T>& (a lattice table in global memory).
+template <typename T, bool MASK, int BXT, typename I, typename PT = KParams<T>>
+__device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restrict__ fout,
+                                           const PT p, int nbands, int seg, int band,
+                                           unsigned char* smem) {
     constexpr int VC = step_cells_per_thread<T>();
     constexpr int W = BXT * VC;          // segment width
     constexpr int SW = W + 2 * kHalo;    // staged row width
     constexpr int RW = W + 8;            // density ring row width
-    extern __shared__ __align__(128) unsigned char smem[];
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem);
     T* stage = reinterpret_cast<T*>(smem + 128);        // [kStages][9][SW]
     T* ring = stage + kStages * 9 * SW;                 // [4][RW], column c at c - x0 + 4
 
     const int tx = threadIdx.x;
     const int lane = tx & 31;
-    const int x0 = blockIdx.x * W;
+    const int x0 = seg * W;
     const int nseg = min(W, p.nx - x0);
     const int c0 = VC * tx;              // first cell of this thread, within the segment
     const int xa = x0 + c0;              // its column
     const bool any_active = c0 < nseg;
     const bool all_active = c0 + VC <= nseg;
-    const int band = blockIdx.y;
     const int y0 = (int)(((long long)band * p.ny) / nbands);
     const int y1 = (int)(((long long)(band + 1) * p.ny) / nbands);
     const int dir = (band & 1) ? -1 : 1;
@@ -381,7 +388,7 @@ rc_step_kernel(const T* __restrict__ fin, T* __restrict__ fout, const KParams<T>
                 for (int j = k; j < k + kStages - 2 && j < nit; ++j)
                     mbar_wait(bar0 + 8u * (j % kStages), (unsigned)((j / kStages) & 1));
             }
-            return;
+            return false;
         }
 
         // 3. refill the stage of row k-2 with row k+2
@@ -419,7 +426,9 @@ rc_step_kernel(const T* __restrict__ fin, T* __restrict__ fout, const KParams<T>
                     const T dN = (b & 8u) ? d : dNv[j];
                     const T dxr = T(0.5) * (dE - dW);
                     const T dyr = p.iah * (dN - dS);
-                    const T rho = p.collide ? collide(p, f, d, dxr, dyr) : p.rho0 + d;
+                    const T rho = !p.collide ? p.rho0 + d
+                                  : p.raw  ? collide_raw(p, f, d, dxr, dyr)
+                                           : collide(p, f, d, dxr, dyr);
                     const int cx = xa + j;
                     if (p.moving && (cx == 0 || cx == p.nx - 1 || edge_row))
                         moving_wall(p, cx, rc, rho, f);
@@ -437,7 +446,111 @@ rc_step_kernel(const T* __restrict__ fin, T* __restrict__ fout, const KParams<T>
         colp = colc;
         rrp = rr;
     }
+    // every copy has been waited for: retire the mbarriers so that the shared
+    // memory can hold new ones (a persistent block runs step_block again)
+    __syncthreads();
+    if (tx == 0)
+        for (int s = 0; s < kStages; ++s) mbar_inval(bar0 + 8u * s);
+    __syncthreads();
+    return true;
 }
+
+// Blocks per SM the register allocator is asked to fit: FP32 at 128 threads
+// is limited to 6 blocks by its shared memory, so registers should allow 6.
+template <typename T>
+constexpr int step_min_blocks(int bxt) {
+    return sizeof(T) == 4 && bxt == 128 ? 6 : sizeof(T) == 4 && bxt == 64 ? 12 : 1;
+}
+
+template <typename T, bool MASK, int BXT, typename I>
+__global__ void __launch_bounds__(BXT, step_min_blocks<T>(BXT))
+rc_step_kernel(const T* __restrict__ fin, T* __restrict__ fout,
+               const __grid_constant__ KParams<T> p, int nbands) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    step_block<T, MASK, BXT, I, const KParams<T>&>(fin, fout, p, nbands, blockIdx.x,
+                                                   blockIdx.y, smem);
+}
+
+// Persistent kernel over many lattices: block b takes work items b,
+// b + gridDim.x, ... of a device work list; item w belongs to the active
+// lattice whose block range [begin, begin + nseg * nbands) holds w.  The
+// lattice's parameters are read from the (read-only) lattice table.
+template <typename T, int BXT>
+__global__ void __launch_bounds__(BXT)
+rc_batch_kernel(const BatchLattice<T>* __restrict__ lat, const int* __restrict__ active,
+                const int* __restrict__ begin, const int* __restrict__ counts, int parity) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int n = counts[0], total = counts[1];
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(begin + mid) <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchLattice<T>* L = lat + __ldg(active + lo);
+        const int local = w - __ldg(begin + lo);
+        const KParams<T>& kp = L->kp;
+        const int nseg = L->nseg;
+        const T* fin = L->f[parity];
+        T* fout = L->f[parity ^ 1];
+        // lattices of a batch stay below 2^31 elements (checked on the host)
+        if (!step_block<T, true, BXT, int, const KParams<T>&>(fin, fout, kp, L->nbands,
+                                                              local % nseg, local / nseg, smem))
+            return;
+    }
+}
+
+template <typename T, int BXT>
+static cudaError_t launch_batch_bx(const BatchLattice<T>* lat, const int* active,
+                                   const int* begin, const int* counts, int parity, int grid,
+                                   cudaStream_t s) {
+    constexpr size_t smem = step_smem_bytes<T, BXT>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(rc_batch_kernel<T, BXT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    rc_batch_kernel<T, BXT><<<grid, BXT, smem, s>>>(lat, active, begin, counts, parity);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batch_step(const BatchLattice<T>* lat, const int* active, const int* begin,
+                              const int* counts, int parity, int bx, int grid,
+                              cudaStream_t s) {
+    switch (bx) {
+    case 32: return launch_batch_bx<T, 32>(lat, active, begin, counts, parity, grid, s);
+    case 64: return launch_batch_bx<T, 64>(lat, active, begin, counts, parity, grid, s);
+    case 128: return launch_batch_bx<T, 128>(lat, active, begin, counts, parity, grid, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+template cudaError_t launch_batch_step<float>(const BatchLattice<float>*, const int*,
+                                              const int*, const int*, int, int, int,
+                                              cudaStream_t);
+
+template <typename T, int BXT>
+static int batch_occ_bx() {
+    constexpr size_t smem = step_smem_bytes<T, BXT>();
+    cudaFuncSetAttribute(rc_batch_kernel<T, BXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rc_batch_kernel<T, BXT>, BXT, smem) !=
+        cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+template <typename T>
+int batch_occupancy(int bx) {
+    return bx == 32 ? batch_occ_bx<T, 32>() : bx == 64 ? batch_occ_bx<T, 64>()
+                                                       : batch_occ_bx<T, 128>();
+}
+template int batch_occupancy<float>(int);
 
 template <typename T, bool MASK, int BXT, typename I>
 static cudaError_t launch_one(const T* fin, T* fout, const KParams<T>& p, int nbands,

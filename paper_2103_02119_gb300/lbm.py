@@ -76,6 +76,7 @@ def _load():
     L.lbm_set_force.argtypes = [_P, ctypes.c_double, ctypes.c_double]
     L.lbm_moments.argtypes = [_P, _P, _P, _P, ctypes.c_int]
     L.lbm_get_f.argtypes = [_P, _P, ctypes.c_int]
+    L.lbm_stress.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int]
     L.lbm_set_f.argtypes = [_P, _P, ctypes.c_int]
     L.lbm_diagnostics.argtypes = [_P, _D]
     L.lbm_diagnostics_noalloc.argtypes = [_P, _D]
@@ -89,6 +90,31 @@ def _load():
     L.lbm_launch_count.restype = ctypes.c_int64
     L.lbm_last_error.argtypes = [_P]
     L.lbm_last_error.restype = ctypes.c_char_p
+    I64 = ctypes.c_int64
+    L.lbm_batch_create.argtypes = [ctypes.POINTER(lbm_params), ctypes.c_int, _P, _P,
+                                   ctypes.POINTER(_P)]
+    L.lbm_batch_destroy.argtypes = [_P]
+    L.lbm_batch_destroy.restype = None
+    L.lbm_batch_count.argtypes = [_P]
+    L.lbm_batch_init_fields.argtypes = [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int]
+    L.lbm_batch_step.argtypes = [_P, I64]
+    L.lbm_batch_residuals.argtypes = [_P, _D]
+    L.lbm_batch_run.argtypes = [_P, ctypes.c_double, I64, I64, _D]
+    L.lbm_batch_set_active.argtypes = [_P, ctypes.c_int, ctypes.c_int]
+    L.lbm_batch_is_active.argtypes = [_P, ctypes.c_int]
+    L.lbm_batch_set_shape.argtypes = [_P, ctypes.c_int, ctypes.c_int]
+    _IP = ctypes.POINTER(ctypes.c_int)
+    L.lbm_batch_get_shape.argtypes = [_P, _IP, _IP]
+    L.lbm_batch_tune.argtypes = [_P, ctypes.c_int, _IP, _IP]
+    L.lbm_batch_moments.argtypes = [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int]
+    L.lbm_batch_get_f.argtypes = [_P, ctypes.c_int, _P, ctypes.c_int]
+    L.lbm_batch_diagnostics.argtypes = [_P, ctypes.c_int, _D]
+    L.lbm_batch_step_count.argtypes = [_P, ctypes.c_int]
+    L.lbm_batch_step_count.restype = I64
+    L.lbm_batch_launch_count.argtypes = [_P]
+    L.lbm_batch_launch_count.restype = I64
+    L.lbm_batch_last_error.argtypes = [_P]
+    L.lbm_batch_last_error.restype = ctypes.c_char_p
     return L
 
 
@@ -187,6 +213,25 @@ def lbm_moments(h, N, rho=None, ux=None, uy=None):
     _check(lib.lbm_moments(h, ptrs[0], ptrs[1], ptrs[2], int(dev)), h)
 
 
+def lbm_stress(h, N, dxux=None, dyuy=None, sxy=None, txx=None, tyy=None, txy=None):
+    """Writes the local strain rates and viscous stress into the given
+    outputs (numpy host arrays or CUDA tensors, float64, N elements)."""
+    outs = (dxux, dyuy, sxy, txx, tyy, txy)
+    dev = _is_device(*outs)
+    ptrs = []
+    for v in outs:
+        if v is None:
+            ptrs.append(None)
+        elif dev:
+            ptrs.append(_arr(v, N, True)[0])
+        else:
+            if not (isinstance(v, np.ndarray) and v.dtype == np.float64
+                    and v.flags.c_contiguous and v.size == N):
+                raise ValueError("host outputs must be contiguous float64 arrays of N elements")
+            ptrs.append(v.ctypes.data)
+    _check(lib.lbm_stress(h, *ptrs, int(dev)), h)
+
+
 def lbm_get_f(h, N, out):
     dev = _is_device(out)
     if dev:
@@ -252,24 +297,269 @@ def lbm_last_error(h=None) -> str:
 
 # ------------------------------------------------------------ convenience --
 
+def make_params(nx, ny, a, cs2, omega, Fx=0.0, Fy=0.0, rho0=1.0, precision=32,
+                periodic_x=1, periodic_y=1, wall_u=None, use_iso_corr=1, use_gi_corr=1,
+                block_x=0, bands=0, scheme=0) -> lbm_params:
+    p = lbm_params_init()
+    p.nx, p.ny, p.a, p.cs2 = int(nx), int(ny), float(a), float(cs2)
+    for j in range(9):
+        p.omega[j] = float(omega[j])
+    p.Fx, p.Fy, p.rho0 = float(Fx), float(Fy), float(rho0)
+    p.precision = int(precision)
+    p.periodic_x, p.periodic_y = int(periodic_x), int(periodic_y)
+    for k in range(4):
+        for d in range(2):
+            p.wall_u[k][d] = 0.0 if wall_u is None else float(wall_u[k][d])
+    p.use_iso_corr, p.use_gi_corr = int(use_iso_corr), int(use_gi_corr)
+    p.block_x, p.bands, p.scheme = int(block_x), int(bands), int(scheme)
+    return p
+
+
+def params_of_workload(wl, precision=32, **kw) -> lbm_params:
+    return make_params(wl.nx, wl.ny, wl.a, wl.cs2, wl.omega, Fx=wl.Fx, Fy=wl.Fy,
+                       precision=precision, periodic_x=wl.periodic_x,
+                       periodic_y=wl.periodic_y, wall_u=wl.wall_u,
+                       use_iso_corr=wl.use_iso_corr, use_gi_corr=wl.use_gi_corr, **kw)
+
+
+# ------------------------------------------------------------- batch ABI --
+
+def _bcheck(status: int, b=None):
+    if status != LBM_OK:
+        raise LbmError(status, lib.lbm_batch_last_error(b).decode())
+
+
+def lbm_batch_create(params, masks=None, stream=None):
+    """params: sequence of lbm_params; masks: None or a sequence of
+    (ny, nx) uint8 arrays / None.  Returns an opaque batch (c_void_p)."""
+    n = len(params)
+    arr = (lbm_params * n)(*params)
+    keep, mptrs = [], None
+    if masks is not None:
+        if len(masks) != n:
+            raise ValueError("one mask (or None) per lattice")
+        mptrs = (ctypes.c_void_p * n)()
+        for k, m in enumerate(masks):
+            if m is None:
+                continue
+            m = np.ascontiguousarray(m, dtype=np.uint8).reshape(-1)
+            if m.size != params[k].nx * params[k].ny:
+                raise ValueError(f"mask {k} must hold nx*ny bytes")
+            keep.append(m)
+            mptrs[k] = m.ctypes.data
+    b = _P()
+    st = lib.lbm_batch_create(arr, n, None if mptrs is None else ctypes.cast(mptrs, _P),
+                              _stream_ptr(stream), ctypes.byref(b))
+    _bcheck(st, None)
+    return b
+
+
+def lbm_batch_destroy(b):
+    lib.lbm_batch_destroy(b)
+
+
+def lbm_batch_count(b) -> int:
+    return int(lib.lbm_batch_count(b))
+
+
+def lbm_batch_init_fields(b, k, N, rho=None, ux=None, uy=None):
+    dev = _is_device(rho, ux, uy)
+    keep = [_arr(v, N, dev) for v in (rho, ux, uy)]
+    _bcheck(lib.lbm_batch_init_fields(b, int(k), keep[0][0], keep[1][0], keep[2][0],
+                                      int(dev)), b)
+
+
+def lbm_batch_step(b, nsteps: int):
+    _bcheck(lib.lbm_batch_step(b, int(nsteps)), b)
+
+
+def lbm_batch_residuals(b, count):
+    """Returns (status, res[count]); LBM_ERR_UNSTABLE is reported, not raised."""
+    out = (ctypes.c_double * count)()
+    st = lib.lbm_batch_residuals(b, out)
+    if st not in (LBM_OK, LBM_ERR_UNSTABLE):
+        _bcheck(st, b)
+    return st, np.array(out[:], dtype=np.float64)
+
+
+def lbm_batch_run(b, count, tol, check_every, max_steps):
+    """Returns (status, res[count]); LBM_ERR_UNSTABLE is reported, not raised."""
+    out = (ctypes.c_double * count)()
+    st = lib.lbm_batch_run(b, float(tol), int(check_every), int(max_steps), out)
+    if st not in (LBM_OK, LBM_ERR_UNSTABLE):
+        _bcheck(st, b)
+    return st, np.array(out[:], dtype=np.float64)
+
+
+def lbm_batch_set_active(b, k, on):
+    _bcheck(lib.lbm_batch_set_active(b, int(k), int(bool(on))), b)
+
+
+def lbm_batch_is_active(b, k) -> int:
+    return int(lib.lbm_batch_is_active(b, int(k)))
+
+
+def lbm_batch_set_shape(b, block_x, rows_per_band):
+    _bcheck(lib.lbm_batch_set_shape(b, int(block_x), int(rows_per_band)), b)
+
+
+def lbm_batch_get_shape(b):
+    bx, rows = ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib.lbm_batch_get_shape(b, ctypes.byref(bx), ctypes.byref(rows)), b)
+    return bx.value, rows.value
+
+
+def lbm_batch_tune(b, trial_steps):
+    bx, rows = ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib.lbm_batch_tune(b, int(trial_steps), ctypes.byref(bx), ctypes.byref(rows)), b)
+    return bx.value, rows.value
+
+
+def lbm_batch_moments(b, k, N, rho=None, ux=None, uy=None):
+    dev = _is_device(rho, ux, uy)
+    ptrs = []
+    for v in (rho, ux, uy):
+        if v is None:
+            ptrs.append(None)
+        elif dev:
+            ptrs.append(_arr(v, N, True)[0])
+        else:
+            if not (isinstance(v, np.ndarray) and v.dtype == np.float64
+                    and v.flags.c_contiguous and v.size == N):
+                raise ValueError("host outputs must be contiguous float64 arrays of N elements")
+            ptrs.append(v.ctypes.data)
+    _bcheck(lib.lbm_batch_moments(b, int(k), ptrs[0], ptrs[1], ptrs[2], int(dev)), b)
+
+
+def lbm_batch_get_f(b, k, N, out):
+    dev = _is_device(out)
+    if dev:
+        ptr = _arr(out, 9 * N, True)[0]
+    else:
+        if not (out.dtype == np.float64 and out.flags.c_contiguous and out.size == 9 * N):
+            raise ValueError("output must be a contiguous float64 array of 9*N elements")
+        ptr = out.ctypes.data
+    _bcheck(lib.lbm_batch_get_f(b, int(k), ptr, int(dev)), b)
+
+
+def lbm_batch_diagnostics(b, k):
+    out = (ctypes.c_double * LBM_DIAG_COUNT)()
+    st = lib.lbm_batch_diagnostics(b, int(k), out)
+    if st not in (LBM_OK, LBM_ERR_UNSTABLE):
+        _bcheck(st, b)
+    return st, np.array(out[:], dtype=np.float64)
+
+
+def lbm_batch_step_count(b, k) -> int:
+    return int(lib.lbm_batch_step_count(b, int(k)))
+
+
+def lbm_batch_launch_count(b) -> int:
+    return int(lib.lbm_batch_launch_count(b))
+
+
+def lbm_batch_last_error(b=None) -> str:
+    return lib.lbm_batch_last_error(b).decode()
+
+
+# ------------------------------------------------------------ convenience --
+
+class Batch:
+    """Many FP32 lattices owned by one batch of the CUDA library."""
+
+    def __init__(self, workloads, stream=None, schemes=None):
+        """schemes: None (all RC-LBM) or one scheme per workload (0 RC-LBM,
+        1 RNR-LBM, -1 no collision)."""
+        if schemes is None:
+            schemes = [0] * len(workloads)
+        self.params = [params_of_workload(w, precision=32, scheme=int(sc))
+                       for w, sc in zip(workloads, schemes)]
+        self.shapes = [(w.ny, w.nx) for w in workloads]
+        self.count = len(workloads)
+        self.b = lbm_batch_create(self.params, [w.mask for w in workloads], stream)
+        for k, w in enumerate(workloads):
+            if w.rho is not None or w.ux is not None or w.uy is not None:
+                self.init_fields(k, w.rho, w.ux, w.uy)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _N(self, k):
+        ny, nx = self.shapes[k]
+        return nx * ny
+
+    def init_fields(self, k, rho=None, ux=None, uy=None):
+        lbm_batch_init_fields(self.b, k, self._N(k), rho, ux, uy)
+
+    def step(self, n=1):
+        lbm_batch_step(self.b, n)
+
+    def residuals(self):
+        return lbm_batch_residuals(self.b, self.count)
+
+    def run(self, tol, check_every=100, max_steps=10**6):
+        return lbm_batch_run(self.b, self.count, tol, check_every, max_steps)
+
+    def set_active(self, k, on):
+        lbm_batch_set_active(self.b, k, on)
+
+    def is_active(self, k) -> bool:
+        return lbm_batch_is_active(self.b, k) == 1
+
+    def set_shape(self, block_x, rows_per_band):
+        lbm_batch_set_shape(self.b, block_x, rows_per_band)
+
+    @property
+    def shape(self):
+        return lbm_batch_get_shape(self.b)
+
+    def tune(self, trial_steps=20):
+        return lbm_batch_tune(self.b, trial_steps)
+
+    def moments(self, k):
+        ny, nx = self.shapes[k]
+        r, u, v = (np.empty((ny, nx)) for _ in range(3))
+        lbm_batch_moments(self.b, k, nx * ny, r, u, v)
+        return r, u, v
+
+    def get_f(self, k):
+        ny, nx = self.shapes[k]
+        f = np.empty((9, ny, nx))
+        lbm_batch_get_f(self.b, k, nx * ny, f)
+        return f
+
+    def diagnostics(self, k):
+        return lbm_batch_diagnostics(self.b, k)
+
+    def step_count(self, k) -> int:
+        return lbm_batch_step_count(self.b, k)
+
+    @property
+    def launch_count(self) -> int:
+        return lbm_batch_launch_count(self.b)
+
+
 class Lattice:
     """A lattice owned by one handle of the CUDA library."""
 
     def __init__(self, nx, ny, a, cs2, omega, Fx=0.0, Fy=0.0, rho0=1.0, precision=32,
                  periodic_x=1, periodic_y=1, wall_u=None, use_iso_corr=1, use_gi_corr=1,
                  mask=None, stream=None, block_x=0, bands=0, scheme=0):
-        p = lbm_params_init()
-        p.nx, p.ny, p.a, p.cs2 = int(nx), int(ny), float(a), float(cs2)
-        for j in range(9):
-            p.omega[j] = float(omega[j])
-        p.Fx, p.Fy, p.rho0 = float(Fx), float(Fy), float(rho0)
-        p.precision = int(precision)
-        p.periodic_x, p.periodic_y = int(periodic_x), int(periodic_y)
-        for k in range(4):
-            for d in range(2):
-                p.wall_u[k][d] = 0.0 if wall_u is None else float(wall_u[k][d])
-        p.use_iso_corr, p.use_gi_corr = int(use_iso_corr), int(use_gi_corr)
-        p.block_x, p.bands, p.scheme = int(block_x), int(bands), int(scheme)
+        p = make_params(nx, ny, a, cs2, omega, Fx=Fx, Fy=Fy, rho0=rho0, precision=precision,
+                        periodic_x=periodic_x, periodic_y=periodic_y, wall_u=wall_u,
+                        use_iso_corr=use_iso_corr, use_gi_corr=use_gi_corr,
+                        block_x=block_x, bands=bands, scheme=scheme)
         self.params = p
         self.nx, self.ny, self.N = p.nx, p.ny, p.nx * p.ny
         self.h = lbm_create(p, mask, stream)
@@ -316,6 +606,12 @@ class Lattice:
         f = np.empty((9, self.ny, self.nx))
         lbm_get_f(self.h, self.N, f)
         return f
+
+    def stress(self):
+        """(d_x u_x, d_y u_y, d_y u_x + d_x u_y, tau_xx, tau_yy, tau_xy)."""
+        out = [np.empty((self.ny, self.nx)) for _ in range(6)]
+        lbm_stress(self.h, self.N, *out)
+        return tuple(out)
 
     def set_f(self, f):
         lbm_set_f(self.h, self.N, f)

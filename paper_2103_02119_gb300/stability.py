@@ -1,0 +1,98 @@
+"""Numerical stability sweeps of the two rectangular schemes (Sec. 6).
+
+Both studies run many small lid-driven cavities at once through the batch
+API of the CUDA library (FP32, one persistent launch per step) and call a
+run unstable when any of its fluid cells turns non-finite within the step
+budget.
+
+* ``lid_velocity_thresholds``: the largest lid speed U that stays stable for
+  a fixed number of steps, against the relaxation time tau, for RC-LBM and
+  RNR-LBM on 21 x ny cavities of physical aspect 1 (ny = 20/a + 1), the
+  study of Fig. 17.
+* ``max_reynolds``: the largest Re = U nx / nu that stays stable at a = 0.5,
+  U = 0.2, c_s^2 = 0.1 on nx x 2nx cavities, the study of Table 6.
+
+The speed of sound of the first study is not given in the paper; it is
+c_s^2 = min(1/3, 0.6 a^2) (1/3 on the square lattice, below a^2 otherwise).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import workloads as W
+
+
+def fig17_cs2(a: float) -> float:
+    return min(1.0 / 3.0, 0.6 * a * a)
+
+
+def _run(wls, schemes, steps, check, stream):
+    from .lbm import Batch
+    b = Batch(wls, stream=stream, schemes=schemes)
+    try:
+        # tol = 0: only a lattice that stops changing exactly is retired early
+        st, res = b.run(0.0, check_every=check, max_steps=steps)
+        done = np.array([b.step_count(k) for k in range(len(wls))])
+    finally:
+        b.close()
+    return ~np.isnan(res), done
+
+
+def lid_velocity_thresholds(a_values=(1.0, 0.5, 0.3), taus=(0.51, 0.55, 0.6, 0.7, 0.8, 1.0),
+                            u_values=None, steps=100_000, check=1000, nx=21, stream=None):
+    """Returns {(a, tau, scheme): largest U of u_values such that it and
+    every smaller U stayed stable}; scheme 0 = RC-LBM, 1 = RNR-LBM."""
+    if u_values is None:
+        u_values = np.round(np.arange(0.02, 0.62, 0.02), 4)
+    wls, schemes, keys = [], [], []
+    for a in a_values:
+        ny = int(round((nx - 1) / a)) + 1
+        cs2 = fig17_cs2(a)
+        for tau in taus:
+            nu = cs2 * (tau - 0.5)
+            for U in u_values:
+                for scheme in (0, 1):
+                    wls.append(W.cavity(nx, ny, a, cs2, float(U), float(U) * nx / nu))
+                    schemes.append(scheme)
+                    keys.append((a, tau, scheme, float(U)))
+    stable, _ = _run(wls, schemes, steps, check, stream)
+    out = {}
+    for (a, tau, scheme, U), ok in zip(keys, stable):
+        out.setdefault((a, tau, scheme), []).append((U, bool(ok)))
+    thr = {}
+    for key, runs in out.items():
+        best = 0.0
+        for U, ok in sorted(runs):
+            if not ok:
+                break
+            best = U
+        thr[key] = best
+    return thr
+
+
+def max_reynolds(grids=((100, 200), (200, 400), (300, 600)), a=0.5, U=0.2, cs2=0.1,
+                 re_values=None, steps=100_000, check=1000, stream=None):
+    """Returns {(nx, ny, scheme): largest Re of re_values such that it and
+    every smaller Re stayed stable}."""
+    if re_values is None:
+        re_values = np.round(np.geomspace(2000, 32000, 17))
+    wls, schemes, keys = [], [], []
+    for nx, ny in grids:
+        for Re in re_values:
+            for scheme in (0, 1):
+                wls.append(W.cavity(nx, ny, a, cs2, U, float(Re)))
+                schemes.append(scheme)
+                keys.append((nx, ny, scheme, float(Re)))
+    stable, _ = _run(wls, schemes, steps, check, stream)
+    out = {}
+    for (nx, ny, scheme, Re), ok in zip(keys, stable):
+        out.setdefault((nx, ny, scheme), []).append((Re, bool(ok)))
+    best = {}
+    for key, runs in out.items():
+        b = 0.0
+        for Re, ok in sorted(runs):
+            if not ok:
+                break
+            b = Re
+        best[key] = b
+    return best

@@ -191,3 +191,54 @@ def perturbation(nx: int, ny: int, seed: int, amp: float = 1e-3) -> np.ndarray:
     non-equilibrium part."""
     rng = np.random.default_rng(seed)
     return amp * rng.standard_normal((9, ny, nx))
+
+
+def batch_sweep(count: int, seed: int = 0, n_range=(64, 1024), a_range=(0.2, 1.0),
+                re_range=(100.0, 5000.0), coverage: float = 0.10,
+                tau_range=(0.505, 2.0)) -> list:
+    """Uneven sweep of independent channel / cavity instances.
+
+    Per instance (seeded): nx, ny = round(exp(U[ln n_min, ln n_max])),
+    a ~ U[a_min, a_max], Re = exp(U[ln Re_min, ln Re_max]); half channels
+    (periodic in x, walls in y, body force), half lid-driven cavities; seeded
+    solid rectangles up to `coverage` with a 2-cell fluid margin.  c_s^2 =
+    stable_cs2(a), U = min(0.05, 0.3 c_s), nu = U nx / Re.  When tau = 1/2 +
+    nu / c_s^2 exceeds tau_max, U is lowered to bring tau to tau_max; when it
+    falls below tau_min the instance is redrawn (the reason is kept in
+    info['redrawn']).  The channel force gives a centre-line speed U in the
+    empty channel (F = 8 nu U / H^2, H = ny a)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    ln = np.log
+    while len(out) < count:
+        nx = int(round(np.exp(rng.uniform(ln(n_range[0]), ln(n_range[1])))))
+        ny = int(round(np.exp(rng.uniform(ln(n_range[0]), ln(n_range[1])))))
+        a = float(rng.uniform(*a_range))
+        Re = float(np.exp(rng.uniform(ln(re_range[0]), ln(re_range[1]))))
+        kind = "channel" if rng.random() < 0.5 else "cavity"
+        mseed = int(rng.integers(1 << 31))
+        cs2 = stable_cs2(a)
+        U = min(0.05, 0.3 * np.sqrt(cs2))
+        nu = U * nx / Re
+        tau = 0.5 + nu / cs2
+        redrawn = None
+        if tau > tau_range[1]:
+            nu = (tau_range[1] - 0.5) * cs2
+            U = nu * Re / nx
+        elif tau < tau_range[0]:
+            redrawn = f"tau {tau:.4f} below {tau_range[0]}"
+        if redrawn:
+            if out:
+                out[-1].info.setdefault("redrawn", []).append(redrawn)
+            continue
+        mask = random_obstacles(nx, ny, seed=mseed, coverage=coverage)
+        if kind == "channel":
+            H = ny * a
+            wl = Workload(f"channel_{nx}x{ny}_a{a:.3f}_Re{Re:.0f}", nx, ny, a, cs2,
+                          omega_for(nu, cs2), Fx=8.0 * nu * U / (H * H), periodic_x=1,
+                          periodic_y=0, mask=mask, info=dict(nu=nu, U=U, Re=Re, kind=kind))
+        else:
+            wl = cavity(nx, ny, a, cs2, U, Re).with_(mask=mask)
+            wl.info["kind"] = kind
+        out.append(wl)
+    return out

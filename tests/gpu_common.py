@@ -36,10 +36,11 @@ def gpu_of(wl, precision, stream=None, **kw):
     return Lattice.from_workload(wl, precision=precision, stream=stream, **kw)
 
 
-def pair(orc, wl, precision, noise_seed=None, noise_amp=1e-3, **kw):
-    """(oracle, gpu) lattices in the same initial state."""
-    o = oracle_of(orc, wl)
-    g = gpu_of(wl, precision, **kw)
+def pair(orc, wl, precision, noise_seed=None, noise_amp=1e-3, scheme=0, **kw):
+    """(oracle, gpu) lattices in the same initial state; scheme 0 = RC-LBM,
+    1 = RNR-LBM."""
+    o = oracle_of(orc, wl, scheme={0: "rc", 1: "rnr"}[scheme])
+    g = gpu_of(wl, precision, scheme=scheme, **kw)
     if noise_seed is not None:
         fluid = 1.0 - o.solid()[None].astype(float)
         n = W.perturbation(wl.nx, wl.ny, noise_seed, noise_amp) * fluid

@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -107,3 +108,40 @@ def test_null_arguments(L):
     assert L.lib.lbm_diagnostics(None, None) == L.LBM_ERR_INVALID
     L.lib.lbm_destroy(None)  # ignored
     assert L.lib.lbm_step_count(None) == -1
+
+
+def test_batch_invalid_params_rejected_on_host(L):
+    good = L.lbm_params_init()
+    bad = L.lbm_params_init()
+    bad.precision = 64
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_batch_create([good, bad])
+    assert e.value.status == L.LBM_ERR_INVALID
+    assert "lattice 1" in str(e.value) and "FP32" in str(e.value)
+    bad = L.lbm_params_init()
+    bad.nx = 2
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_batch_create([bad, good])
+    assert "lattice 0" in str(e.value) and "nx and ny" in str(e.value)
+    big = L.lbm_params_init()
+    big.nx, big.ny = 65536, 4096          # 9 x 65536 x 4096 >= 2^31 values
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_batch_create([good, big])
+    assert "2^31" in str(e.value)
+    with pytest.raises(ValueError):
+        L.lbm_batch_create([good], masks=[np.zeros(5, np.uint8)])
+
+
+def test_batch_null_arguments(L):
+    p = L.lbm_params_init()
+    out = ctypes.c_void_p()
+    assert L.lib.lbm_batch_create(ctypes.byref(p), 1, None, None, None) == L.LBM_ERR_INVALID
+    assert L.lib.lbm_batch_create(None, 1, None, None, ctypes.byref(out)) == L.LBM_ERR_INVALID
+    assert L.lib.lbm_batch_create(ctypes.byref(p), 0, None, None, ctypes.byref(out)) == \
+        L.LBM_ERR_INVALID
+    assert L.lib.lbm_batch_step(None, 1) == L.LBM_ERR_INVALID
+    assert L.lib.lbm_batch_run(None, 1e-8, 100, 100, None) == L.LBM_ERR_INVALID
+    assert L.lib.lbm_batch_count(None) == -1
+    assert L.lib.lbm_batch_is_active(None, 0) == -1
+    assert L.lib.lbm_batch_step_count(None, 0) == -1
+    L.lib.lbm_batch_destroy(None)  # ignored

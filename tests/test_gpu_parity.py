@@ -63,6 +63,20 @@ def test_parity(orc, name, precision):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+def test_parity_raw_moment_scheme(orc, name, precision):
+    """The raw-moment scheme (RNR-LBM, Sec. 3) against the oracle's."""
+    wl = CONFIGS[name]
+    o, g = pair(orc, wl, precision, noise_seed=12, noise_amp=5e-4, scheme=1)
+    o.step(9)
+    g.step(9)
+    compare(o, g, precision)
+    o.step(11)
+    g.step(11)
+    compare(o, g, precision)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("block_x,bands", [(32, 1), (32, 67), (64, 5), (256, 2), (128, 33)])
 def test_tilings_are_bit_identical(precision, block_x, bands):
     """The result does not depend on how the step kernel is tiled: every cell
@@ -251,3 +265,25 @@ def test_state_size_mismatch_is_rejected():
     with pytest.raises(lbm.LbmError) as e:
         g.set_state(b"\0" * 8)
     assert e.value.status == lbm.LBM_ERR_STATE
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("name", ["channel_force", "obstacles_lid_a025", "a2_force_xy",
+                                  "tgv_ragged", "tiny_5x7_mask"])
+def test_stress_output_matches_oracle(orc, name, precision):
+    """Local strain rates and viscous stress (Eq. 30-40) of the same state:
+    the GPU state is copied into the oracle, so that only the order of the
+    FP64 arithmetic differs."""
+    wl = CONFIGS[name]
+    o, g = pair(orc, wl, precision, noise_seed=15, noise_amp=5e-4)
+    g.step(17)
+    o.set_f(g.get_f())
+    sx, sy = o.strain()
+    sxy, txx, tyy, txy = o.stress()
+    got = g.stress()
+    for ref, val in zip((sx, sy, sxy, txx, tyy, txy), got):
+        scale = max(float(np.abs(ref).max()), 1e-300)
+        assert float(np.abs(val - ref).max()) <= 1e-8 * scale
+    solid = o.solid().astype(bool)
+    for val in got:
+        assert np.all(val[solid] == 0.0)

@@ -145,3 +145,56 @@ def test_local_strain_rates_converge_to_velocity_gradient(orc, a):
     for c in range(2):
         assert errs[1][c] / errs[2][c] > 3.0, errs
         assert errs[2][c] < 0.02, errs
+
+
+@pytest.mark.parametrize("a,direction", [(0.5, "x"), (0.25, "x"), (0.5, "y"), (0.25, "y")])
+def test_off_diagonal_strain_converges_to_velocity_gradient(orc, a, direction):
+    """Eq. 39 (left side read as d_y u_x + d_x u_y, the rate that Eq. 21 ties
+    to m5) against the spectral derivatives of the velocity of a decaying
+    shear wave: second-order convergence; the stress output is the
+    Newtonian stress of Eq. 30-33 built from the three local rates."""
+    cs2 = W.stable_cs2(a)
+    errs = []
+    for nx in (16, 32, 64):
+        wl = W.shear_wave(nx, int(round(nx / a)), a, cs2, nu=0.05, direction=direction,
+                          u0=0.01, seed=2)
+        o = orc.Oracle(orc.OracleParams.make(wl.nx, wl.ny, a, cs2, wl.omega))
+        o.init_fields(wl.rho, wl.ux, wl.uy)
+        o.step(int(50 * (nx / 16) ** 2 / 4) + 10)
+        r, u, v = o.moments()
+        sxy, txx, tyy, txy = o.stress()
+        kx = 2 * np.pi * np.fft.fftfreq(wl.nx, 1.0)
+        ky = 2 * np.pi * np.fft.fftfreq(wl.ny, a)
+        dudy = np.real(np.fft.ifft2(1j * ky[:, None] * np.fft.fft2(u)))
+        dvdx = np.real(np.fft.ifft2(1j * kx[None, :] * np.fft.fft2(v)))
+        ref = dudy + dvdx
+        errs.append(np.abs(sxy - ref).max() / np.abs(ref).max())
+        # stress from the rates: nu = cs2 (1/omega - 1/2) (Eq. 32-33)
+        nu = cs2 * (1 / wl.omega[4] - 0.5)
+        zeta = cs2 * (1 / wl.omega[3] - 0.5)
+        sx, sy = o.strain()
+        div = sx + sy
+        assert np.allclose(txy, r * nu * sxy, rtol=1e-13, atol=0)
+        assert np.allclose(txx, r * (nu * (2 * sx - div) + zeta * div), rtol=1e-12, atol=1e-18)
+        assert np.allclose(tyy, r * (nu * (2 * sy - div) + zeta * div), rtol=1e-12, atol=1e-18)
+    assert errs[1] / errs[2] > 3.0, errs
+    assert errs[2] < 0.02, errs
+
+
+def test_shear_stress_of_steady_channels_is_linear(orc):
+    """Steady body-force channel (Sec. 5.1): the local shear stress is the
+    exact linear profile tau_xy = -F (y - H/2) (momentum balance), and the
+    normal stresses vanish."""
+    for a in (0.5, 0.25):
+        wl = W.poiseuille(ny=24, nx=4, a=a, cs2=W.stable_cs2(a), nu=0.1, U=0.01)
+        o = orc.Oracle(orc.OracleParams.make(wl.nx, wl.ny, a, wl.cs2, wl.omega, Fx=wl.Fx,
+                                             periodic_x=1, periodic_y=0))
+        o.step(int(6 * (wl.ny * a) ** 2 / 0.1))
+        sxy, txx, tyy, txy = o.stress()
+        H = wl.ny * a
+        y = (np.arange(wl.ny) + 0.5) * a
+        exact = -wl.Fx * (y - H / 2)
+        prof = txy[:, 0]
+        assert np.abs(prof - exact).max() < 0.02 * np.abs(exact).max(), (a, prof, exact)
+        assert np.abs(txx).max() < 1e-2 * np.abs(exact).max()
+        assert np.abs(tyy).max() < 1e-2 * np.abs(exact).max()
