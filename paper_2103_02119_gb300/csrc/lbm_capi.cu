@@ -14,6 +14,7 @@
 #include "lbm_launch.h"
 
 using lbm::AuxParams;
+using lbm::CollConst;
 using lbm::DiagPartial;
 using lbm::KParams;
 
@@ -128,6 +129,14 @@ const char* validate(const lbm_params* p) {
     return nullptr;
 }
 
+// A constant as a lane value of the collision (FP32: both halves of a float2).
+template <typename T>
+typename lbm::Lane<T>::V lane_of(double v);
+template <>
+float2 lane_of<float>(double v) { return make_float2((float)v, (float)v); }
+template <>
+double lane_of<double>(double v) { return v; }
+
 // Storage geometry of one lattice.
 struct Geometry {
     int pitch;
@@ -157,39 +166,54 @@ KParams<T> kparams_of(const lbm_params& q, const Geometry& g) {
     const double a = q.a, cs2 = q.cs2, a2 = a * a;
     k.a = T(a);
     k.iah = T(0.5 / a);
-    k.ia2 = T(1.0 / a2);
     k.iah2 = T(0.5 / a2);
-    k.a2 = T(a2);
     k.cs2 = T(cs2);
-    k.cs4 = T(cs2 * cs2);
     k.rho0 = T(q.rho0);
     const double* w = q.omega;
-    k.w3 = T(w[3]);
-    k.w4 = T(w[4]);
-    k.w5 = T(w[5]);
-    k.w6 = T(w[6]);
-    k.w7 = T(w[7]);
-    k.w8 = T(w[8]);
-    k.lw3 = T(1.0 - 0.5 * w[3]);
-    k.lw4 = T(1.0 - 0.5 * w[4]);
-    k.lw5 = T(1.0 - 0.5 * w[5]);
-    k.lw6 = T(1.0 - 0.5 * w[6]);
-    k.lw7 = T(1.0 - 0.5 * w[7]);
-    k.lw8 = T(1.0 - 0.5 * w[8]);
     const double g1 = 1.0 - 3.0 * cs2, g2 = a2 - 3.0 * cs2;
-    k.g1i = T(q.use_iso_corr ? g1 : 0.0);
-    k.g2i = T(q.use_iso_corr ? g2 : 0.0);
-    k.g3 = T(q.use_gi_corr ? 3.0 : 0.0);
-    k.g1h = T(0.5 * g1);
-    k.g2h = T(0.5 * g2);
-    k.b1c = T(-2.0 * cs2 / w[3] - 0.5 * g1);
-    k.b2c = T(-2.0 * cs2 / w[3] - 0.5 * g2);
-    k.c1c = T(-2.0 * cs2 / w[4] - 0.5 * g1);
-    k.c2c = T(2.0 * cs2 / w[4] + 0.5 * g2);
-    k.Fx = T(q.Fx);
-    k.Fy = T(q.Fy);
-    k.hFx = T(0.5 * q.Fx);
-    k.hFy = T(0.5 * q.Fy);
+    CollConst<T>& c = k.cc;
+    auto L = [](double v) { return lane_of<T>(v); };
+    c.rho0 = L(q.rho0);
+    c.nrho0 = L(-q.rho0);
+    c.a = L(a);
+    c.a2 = L(a2);
+    c.cs2 = L(cs2);
+    c.cs4 = L(cs2 * cs2);
+    c.Fx = L(q.Fx);
+    c.Fy = L(q.Fy);
+    c.hFx = L(0.5 * q.Fx);
+    c.hFy = L(0.5 * q.Fy);
+    c.twoFx = L(2.0 * q.Fx);
+    c.twoFy = L(2.0 * q.Fy);
+    c.half = L(0.5);
+    c.two = L(2.0);
+    c.c15 = L(1.5);
+    c.nc15 = L(-1.5);
+    c.b1c = L(-2.0 * cs2 / w[3] - 0.5 * g1);
+    c.b2c = L(-2.0 * cs2 / w[3] - 0.5 * g2);
+    c.c1c = L(-2.0 * cs2 / w[4] - 0.5 * g1);
+    c.c2c = L(2.0 * cs2 / w[4] + 0.5 * g2);
+    c.g1h = L(0.5 * g1);
+    c.g2h = L(0.5 * g2);
+    c.g1i = L(q.use_iso_corr ? g1 : 0.0);
+    c.g2i = L(q.use_iso_corr ? g2 : 0.0);
+    c.ng3 = L(q.use_gi_corr ? -3.0 : 0.0);
+    c.lw3 = L(1.0 - 0.5 * w[3]);
+    c.lw4 = L(1.0 - 0.5 * w[4]);
+    c.lw5 = L(1.0 - 0.5 * w[5]);
+    c.lw6 = L(1.0 - 0.5 * w[6]);
+    c.lw7 = L(1.0 - 0.5 * w[7]);
+    c.lw8 = L(1.0 - 0.5 * w[8]);
+    c.nw3 = L(-w[3]);
+    c.nw4 = L(-w[4]);
+    c.nw5 = L(-w[5]);
+    c.nw6 = L(-w[6]);
+    c.nw7 = L(-w[7]);
+    c.nw8 = L(-w[8]);
+    c.iah = L(0.5 / a);
+    c.niah = L(-0.5 / a);
+    c.iah2 = L(0.5 / a2);
+    c.nia2 = L(-1.0 / a2);
     k.lmask = g.lmask;
     k.collide = q.scheme >= 0;
     k.raw = q.scheme == 1;

@@ -30,6 +30,26 @@ __host__ __device__ constexpr int opp(int i) {
     return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
 }
 
+template <typename T> struct Lane;
+template <> struct Lane<float> { using V = float2; };
+template <> struct Lane<double> { using V = double; };
+
+// Constants of the collision, each held as a lane value (FP32: the same
+// value in both halves of a float2), computed once on the host.
+template <typename T>
+struct CollConst {
+    using V = typename Lane<T>::V;
+    V rho0, nrho0, a, a2, cs2, cs4;
+    V Fx, Fy, hFx, hFy, twoFx, twoFy;  // force, half force, twice the force
+    V half, two, c15, nc15;            // 1/2, 2, 3/2, -3/2
+    V b1c, b2c, c1c, c2c;              // rho-free, u-free parts of B1, B2, C1, C2 (Eq. 40)
+    V g1h, g2h;                        // (1 - 3cs2)/2, (a^2 - 3cs2)/2 (strain solve)
+    V g1i, g2i, ng3;                   // iso (1 - 3cs2), iso (a^2 - 3cs2), -3 gi
+    V lw3, lw4, lw5, lw6, lw7, lw8;    // 1 - w_j/2
+    V nw3, nw4, nw5, nw6, nw7, nw8;    // -w_j
+    V iah, niah, iah2, nia2;           // 1/(2a), -1/(2a), 1/(2a^2), -1/a^2
+};
+
 // Kernel parameters, converted once on the host to the arithmetic type T.
 template <typename T>
 struct KParams {
@@ -40,18 +60,11 @@ struct KParams {
     int moving;               // some wall moves
     int collide;              // 0: streaming and bounce-back only
     int raw;                  // 1: raw-moment collision (RNR-LBM, Sec. 3)
-    T a, iah, ia2, iah2;      // a, 1/(2a), 1/a^2, 1/(2a^2)
-    T a2, cs2, cs4, rho0;
-    T w3, w4, w5, w6, w7, w8; // relaxation rates
-    T lw3, lw4;               // w_j (1/w_j - 1/2) = 1 - w_j/2
-    T lw5, lw6, lw7, lw8;     // 1 - w_j/2 (raw source moments, RNR-LBM)
-    T g1i, g2i, g3;           // iso * (1 - 3cs2), iso * (a^2 - 3cs2), gi * 3
-    T g1h, g2h;               // (1 - 3cs2)/2, (a^2 - 3cs2)/2 (strain solve)
-    T b1c, b2c, c1c, c2c;     // rho-free, u-free parts of B1, B2, C1, C2 (Eq. 40)
-    T Fx, Fy, hFx, hFy;       // force and half force
+    T a, iah, iah2, cs2, rho0;  // a, 1/(2a), 1/(2a^2), c_s^2, rho0
     T wall_u[4][2];
     const uint8_t* __restrict__ lmask;  // per-cell link mask (nullable)
     int* status;                        // bit 0: a bounded wait ran out
+    CollConst<T> cc;                    // constants of the collision
 };
 
 // Host/device double-precision parameters for the auxiliary kernels.
@@ -104,11 +117,6 @@ __device__ __forceinline__ void pull(const S* __restrict__ fin, const P& p, int 
     f[8] = __ldg(fin + ((sb & 128u) ? 6 * pl + c : 8 * pl + rp + xm));
 }
 
-// Reciprocal used by the collision: FP32 takes the hardware approximation
-// (at most 2 ulp off, below the FP32 storage rounding), FP64 an IEEE division.
-__device__ __forceinline__ float rcp(float v) { return __fdividef(1.0f, v); }
-__device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
-
 // 1-D three-velocity Maxwell-matched factors of the equilibrium
 // f_i^eq = rho phi_x(e_ix, u_x) phi_y(e_iy, u_y) (the tensor-product form of
 // T^-1 F(-u) m^{c,eqr}).
@@ -130,7 +138,30 @@ __device__ __forceinline__ T eq_odd(int k, T rho, T Ux, T Uy, T cs2, T a, T iah2
                   phi_x<T>(-sx, Ux, cs2) * phi_y<T>(-sy, Uy, cs2, a, iah2));
 }
 
-// Collision of one cell (Sec. 4) in increment form on deviations:
+// Lane arithmetic of the collision.  FP32 collides the two cells a thread
+// owns as one float2 through the packed FP32 instructions of sm_100 and
+// later (add, multiply and fused multiply-add on both cells at once); FP64
+// collides one cell per double.  Every operation is written out, so the
+// rounding of a cell does not depend on how the compiler would have
+// contracted an expression, nor on which lane or block computes it.
+__device__ __forceinline__ double vadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double vsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double vmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double vneg(double a) { return -a; }
+__device__ __forceinline__ double vrcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, vneg(b)); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// FP32: the hardware reciprocal approximation (at most 2 ulp off, below the
+// FP32 storage rounding); FP64: an IEEE division.
+__device__ __forceinline__ float2 vrcp(float2 a) {
+    return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y));
+}
+
+// Collision of one lane (Sec. 4) in increment form on deviations:
 //   f~ = f + T^-1 F(-u) [ Lambda (m^{c,eq} - m^c) + (I - Lambda/2) Phi^c ].
 // The D2Q9 basis of Eq. 3 is the tensor product {1, x, x^2} x {1, y, y^2},
 // so T, F(u) and their inverses factor into 3x3 maps along x and along y:
@@ -140,115 +171,126 @@ __device__ __forceinline__ T eq_odd(int k, T rho, T Ux, T Uy, T cs2, T a, T iah2
 //   f: deviations in, post-collision deviations out.  d = sum f (density
 //   deviation).  dxr, dyr: density gradient.  Returns rho.
 template <typename T>
-__device__ __forceinline__ T collide(const KParams<T>& p, T f[9], T d, T dxr, T dyr) {
-    const T rho = p.rho0 + d;
-    const T jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
-    const T jy = p.a * ((f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]));
-    const T ir = rcp(rho);
-    const T ux = (jx + p.hFx) * ir;
-    const T uy = (jy + p.hFy) * ir;
-    const T a = p.a, a2 = p.a2, cs2 = p.cs2;
+__device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
+                                                       typename Lane<T>::V f[9],
+                                                       typename Lane<T>::V d,
+                                                       typename Lane<T>::V dxr,
+                                                       typename Lane<T>::V dyr) {
+    using V = typename Lane<T>::V;
+    const V rho = vadd(c.rho0, d);
+    const V jx = vsub(vadd(vadd(f[1], f[5]), f[8]), vadd(vadd(f[3], f[6]), f[7]));
+    const V jy = vmul(c.a, vsub(vadd(vadd(f[2], f[5]), f[6]), vadd(vadd(f[4], f[7]), f[8])));
+    const V ir = vrcp(rho);
+    const V ux = vmul(vadd(jx, c.hFx), ir);
+    const V uy = vmul(vadd(jy, c.hFy), ir);
+    const V nux = vneg(ux), nuy = vneg(uy);
 
     // Central moments along y of each column e_x = 0, +1, -1:
     // k0 = sum g, k1 = sum g (e_y - u_y), k2 = sum g (e_y - u_y)^2.
-    T k0[3], k1[3], k2[3];
+    V k0[3], k1[3], k2[3];
     {
-        const T gz[3] = {f[0], f[1], f[3]}, gp[3] = {f[2], f[5], f[6]},
+        const V gz[3] = {f[0], f[1], f[3]}, gp[3] = {f[2], f[5], f[6]},
                 gm[3] = {f[4], f[8], f[7]};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const T s = gp[c] + gm[c], dd = gp[c] - gm[c];
-            k0[c] = gz[c] + s;
-            k1[c] = a * dd - uy * k0[c];
-            k2[c] = a2 * s - uy * (k1[c] + a * dd);
+        for (int q = 0; q < 3; ++q) {
+            const V s = vadd(gp[q], gm[q]), dd = vsub(gp[q], gm[q]);
+            k0[q] = vadd(gz[q], s);
+            k1[q] = vfma(nuy, k0[q], vmul(c.a, dd));
+            k2[q] = vfma(nuy, vfma(c.a, dd, k1[q]), vmul(c.a2, s));
         }
     }
     // Along x: C[p][q] = sum_X (e_x - u_x)^p k_q(X).
-    T C[3][3];
+    V C[3][3];
     {
-        const T* kq[3] = {k0, k1, k2};
+        const V* kq[3] = {k0, k1, k2};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            const T S = kq[q][1] + kq[q][2], D = kq[q][1] - kq[q][2];
-            C[0][q] = kq[q][0] + S;
-            C[1][q] = D - ux * C[0][q];
-            C[2][q] = S - ux * (C[1][q] + D);
+            const V S = vadd(kq[q][1], kq[q][2]), D = vsub(kq[q][1], kq[q][2]);
+            C[0][q] = vadd(kq[q][0], S);
+            C[1][q] = vfma(nux, C[0][q], D);
+            C[2][q] = vfma(nux, vadd(C[1][q], D), S);
         }
     }
     // Non-equilibrium central moments: subtract the Maxwell-matched values
     // (rho cs2 on xx and yy, rho cs2^2 on xxyy) and add back the central
     // moments of rho0 w about u.
-    const T ux2 = ux * ux, uy2 = uy * uy;
-    const T r0 = p.rho0;
-    const T n20 = C[2][0] + r0 * ux2 - d * cs2;
-    const T n02 = C[0][2] + r0 * uy2 - d * cs2;
-    const T n11 = C[1][1] + r0 * ux * uy;
-    const T n21 = C[2][1] - r0 * uy * (cs2 + ux2);
-    const T n12 = C[1][2] - r0 * ux * (cs2 + uy2);
-    const T n22 = C[2][2] + r0 * (cs2 * (ux2 + uy2) + ux2 * uy2) - d * p.cs4;
-    const T k3 = n20 + n02, k4 = n20 - n02;
+    const V ux2 = vmul(ux, ux), uy2 = vmul(uy, uy);
+    const V nd = vneg(d);
+    const V n20 = vfma(c.rho0, ux2, vfma(nd, c.cs2, C[2][0]));
+    const V n02 = vfma(c.rho0, uy2, vfma(nd, c.cs2, C[0][2]));
+    const V n11 = vfma(vmul(c.rho0, ux), uy, C[1][1]);
+    const V n21 = vfma(vmul(c.nrho0, uy), vadd(c.cs2, ux2), C[2][1]);
+    const V n12 = vfma(vmul(c.nrho0, ux), vadd(c.cs2, uy2), C[1][2]);
+    const V n22 = vfma(c.rho0, vfma(c.cs2, vadd(ux2, uy2), vmul(ux2, uy2)),
+                       vfma(nd, c.cs4, C[2][2]));
+    const V k3 = vadd(n20, n02), k4 = vsub(n20, n02);
 
     // Local strain rates, Eq. 37-38, from the raw non-equilibrium moments of
     // Eq. 34-35 (central ones minus the force terms u.F).
-    const T N3 = k3 - (ux * p.Fx + uy * p.Fy);
-    const T N4 = k4 - (ux * p.Fx - uy * p.Fy);
-    const T b1 = p.b1c + T(1.5) * ux2, b2 = p.b2c + T(1.5) * uy2;
-    const T c1 = p.c1c + T(1.5) * ux2, c2 = p.c2c - T(1.5) * uy2;
-    const T gx = p.g1h * ux * dxr, gy = p.g2h * uy * dyr;
-    const T R3 = N3 + gx + gy;
-    const T R4 = N4 + gx - gy;
-    const T idet = rcp(rho * (b1 * c2 - b2 * c1));
-    const T dxux = (c2 * R3 - b2 * R4) * idet;
-    const T dyuy = (b1 * R4 - c1 * R3) * idet;
+    const V uFy = vmul(uy, c.Fy);
+    const V N3 = vsub(k3, vfma(ux, c.Fx, uFy));
+    const V N4 = vsub(k4, vsub(vmul(ux, c.Fx), uFy));
+    const V b1 = vfma(c.c15, ux2, c.b1c), b2 = vfma(c.c15, uy2, c.b2c);
+    const V c1 = vfma(c.c15, ux2, c.c1c), c2 = vfma(c.nc15, uy2, c.c2c);
+    const V gx = vmul(vmul(c.g1h, ux), dxr), gy = vmul(vmul(c.g2h, uy), dyr);
+    const V R3 = vadd(vadd(N3, gx), gy);
+    const V R4 = vsub(vadd(N4, gx), gy);
+    const V idet = vrcp(vmul(rho, vfma(b1, c2, vmul(vneg(b2), c1))));
+    const V dxux = vmul(vfma(c2, R3, vmul(vneg(b2), R4)), idet);
+    const V dyuy = vmul(vfma(b1, R4, vmul(vneg(c1), R3)), idet);
 
     // Corrections, Eq. 23-26: m3s + m3G = l3 (Px + Py), m4s + m4G = l4 (Px - Py).
-    const T Px = p.g1i * (rho * dxux + ux * dxr) - p.g3 * rho * ux2 * dxux;
-    const T Py = p.g2i * (rho * dyuy + uy * dyr) - p.g3 * rho * uy2 * dyuy;
+    const V rdx = vmul(rho, dxux), rdy = vmul(rho, dyuy);
+    const V Px = vfma(c.g1i, vfma(ux, dxr, rdx), vmul(vmul(c.ng3, rdx), ux2));
+    const V Py = vfma(c.g2i, vfma(uy, dyr, rdy), vmul(vmul(c.ng3, rdy), uy2));
 
     // Relaxation (Eq. 49 equilibria, Phi^c = (0, Fx, Fy, 0, ...)):
     // increments of the central moments.  kappa_1 = -Fx/2 before collision,
     // so its increment is Fx whatever omega_1 (same for y).
-    const T dk3 = p.lw3 * (Px + Py) - p.w3 * k3;
-    const T dk4 = p.lw4 * (Px - Py) - p.w4 * k4;
-    const T D20 = T(0.5) * (dk3 + dk4), D02 = T(0.5) * (dk3 - dk4);
-    const T D11 = -p.w5 * n11, D21 = -p.w6 * n21, D12 = -p.w7 * n12,
-            D22 = -p.w8 * n22;
+    const V dk3 = vfma(c.lw3, vadd(Px, Py), vmul(c.nw3, k3));
+    const V dk4 = vfma(c.lw4, vsub(Px, Py), vmul(c.nw4, k4));
+    const V D20 = vmul(c.half, vadd(dk3, dk4)), D02 = vmul(c.half, vsub(dk3, dk4));
+    const V D11 = vmul(c.nw5, n11), D21 = vmul(c.nw6, n21), D12 = vmul(c.nw7, n12),
+            D22 = vmul(c.nw8, n22);
 
-    // Back along x: central -> raw x-moments -> the three columns, for each q.
-    T h[3][3];  // h[X][q], X = 0, +1, -1
+    // Back along x: central -> raw x-moments -> the three columns (h[X][q],
+    // X = 0, +1, -1), for q = 0: (0, Fx, D20), q = 1: (Fy, D11, D21),
+    // q = 2: (D02, D12, D22).
+    V h[3][3];
     {
-        const T Dq0[3] = {T(0), p.Fx, D20};
-        const T Dq1[3] = {p.Fy, D11, D21};
-        const T Dq2[3] = {D02, D12, D22};
-        const T* Dq[3] = {Dq0, Dq1, Dq2};
+        const V m2 = vfma(ux, c.twoFx, D20);  // m0 = 0, m1 = Fx
+        h[0][0] = vneg(m2);
+        h[1][0] = vmul(c.half, vadd(m2, c.Fx));
+        h[2][0] = vmul(c.half, vsub(m2, c.Fx));
+    }
+    {
+        const V m0[2] = {c.Fy, D02}, m1in[2] = {D11, D12}, m2in[2] = {D21, D22};
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const T m0 = Dq[q][0];
-            const T m1 = Dq[q][1] + ux * m0;
-            const T m2 = Dq[q][2] + ux * (Dq[q][1] + m1);
-            h[0][q] = m0 - m2;
-            h[1][q] = T(0.5) * (m2 + m1);
-            h[2][q] = T(0.5) * (m2 - m1);
+        for (int q = 1; q < 3; ++q) {
+            const V m1 = vfma(ux, m0[q - 1], m1in[q - 1]);
+            const V m2 = vfma(ux, vadd(m1in[q - 1], m1), m2in[q - 1]);
+            h[0][q] = vsub(m0[q - 1], m2);
+            h[1][q] = vmul(c.half, vadd(m2, m1));
+            h[2][q] = vmul(c.half, vsub(m2, m1));
         }
     }
     // Back along y for each column, and add the increment.
     {
         const int iz[3] = {0, 1, 3}, ip[3] = {2, 5, 6}, im[3] = {4, 8, 7};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const T m0 = h[c][0];
-            const T m1 = h[c][1] + uy * m0;
-            const T m2 = h[c][2] + uy * (h[c][1] + m1);
-            const T t2 = p.iah2 * m2, t1 = p.iah * m1;
-            f[iz[c]] += m0 - p.ia2 * m2;
-            f[ip[c]] += t2 + t1;
-            f[im[c]] += t2 - t1;
+        for (int X = 0; X < 3; ++X) {
+            const V m0 = h[X][0];
+            const V m1 = vfma(uy, m0, h[X][1]);
+            const V m2 = vfma(uy, vadd(h[X][1], m1), h[X][2]);
+            f[iz[X]] = vadd(f[iz[X]], vfma(c.nia2, m2, m0));
+            f[ip[X]] = vfma(c.iah2, m2, vfma(c.iah, m1, f[ip[X]]));
+            f[im[X]] = vfma(c.iah2, m2, vfma(c.niah, m1, f[im[X]]));
         }
     }
     return rho;
 }
 
-// Collision of one cell of the raw-moment scheme (RNR-LBM, Sec. 3), in the
+// Collision of one lane of the raw-moment scheme (RNR-LBM, Sec. 3), in the
 // increment form of collide():
 //   f~ = f + T^-1 [ Lambda (m^eq - m) + (I - Lambda/2) Phi ]
 // with the raw equilibria of Eq. 12 (m^eq_8 = rho cs2^2 + rho cs2 |u|^2 +
@@ -258,98 +300,101 @@ __device__ __forceinline__ T collide(const KParams<T>& p, T f[9], T d, T dxr, T 
 // the transforms are those of collide() at u = 0.  The strain rates
 // (Eq. 37-38) and corrections are the same as in collide().
 template <typename T>
-__device__ __forceinline__ T collide_raw(const KParams<T>& p, T f[9], T d, T dxr, T dyr) {
-    const T rho = p.rho0 + d;
-    const T jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
-    const T jy = p.a * ((f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]));
-    const T ir = rcp(rho);
-    const T ux = (jx + p.hFx) * ir;
-    const T uy = (jy + p.hFy) * ir;
-    const T a = p.a, a2 = p.a2, cs2 = p.cs2;
+__device__ __forceinline__ typename Lane<T>::V collide_raw(const CollConst<T>& c,
+                                                           typename Lane<T>::V f[9],
+                                                           typename Lane<T>::V d,
+                                                           typename Lane<T>::V dxr,
+                                                           typename Lane<T>::V dyr) {
+    using V = typename Lane<T>::V;
+    const V rho = vadd(c.rho0, d);
+    const V jx = vsub(vadd(vadd(f[1], f[5]), f[8]), vadd(vadd(f[3], f[6]), f[7]));
+    const V jy = vmul(c.a, vsub(vadd(vadd(f[2], f[5]), f[6]), vadd(vadd(f[4], f[7]), f[8])));
+    const V ir = vrcp(rho);
+    const V ux = vmul(vadd(jx, c.hFx), ir);
+    const V uy = vmul(vadd(jy, c.hFy), ir);
 
     // Raw moments along y of each column: k0 = sum g, k1 = sum g e_y,
     // k2 = sum g e_y^2; then along x: R[p][q] = sum_X e_x^p k_q(X).
-    T k0[3], k1[3], k2[3];
+    V k0[3], k1[3], k2[3];
     {
-        const T gz[3] = {f[0], f[1], f[3]}, gp[3] = {f[2], f[5], f[6]},
+        const V gz[3] = {f[0], f[1], f[3]}, gp[3] = {f[2], f[5], f[6]},
                 gm[3] = {f[4], f[8], f[7]};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const T sum = gp[c] + gm[c];
-            k0[c] = gz[c] + sum;
-            k1[c] = a * (gp[c] - gm[c]);
-            k2[c] = a2 * sum;
+        for (int q = 0; q < 3; ++q) {
+            const V s = vadd(gp[q], gm[q]);
+            k0[q] = vadd(gz[q], s);
+            k1[q] = vmul(c.a, vsub(gp[q], gm[q]));
+            k2[q] = vmul(c.a2, s);
         }
     }
-    T R[3][3];
+    V R[3][3];
     {
-        const T* kq[3] = {k0, k1, k2};
+        const V* kq[3] = {k0, k1, k2};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            const T S = kq[q][1] + kq[q][2];
-            R[0][q] = kq[q][0] + S;
-            R[1][q] = kq[q][1] - kq[q][2];
+            const V S = vadd(kq[q][1], kq[q][2]);
+            R[0][q] = vadd(kq[q][0], S);
+            R[1][q] = vsub(kq[q][1], kq[q][2]);
             R[2][q] = S;
         }
     }
     // Non-equilibrium raw moments m - m^{eq,r} (Eq. 12); the stored values
     // are deviations from rho0 w, whose raw moments are rho0 cs2 on xx and
     // yy and rho0 cs2^2 on xxyy.
-    const T ux2 = ux * ux, uy2 = uy * uy;
-    const T n20 = R[2][0] - d * cs2 - rho * ux2;
-    const T n02 = R[0][2] - d * cs2 - rho * uy2;
-    const T n11 = R[1][1] - rho * ux * uy;
-    const T n21 = R[2][1] - rho * uy * (cs2 + ux2);
-    const T n12 = R[1][2] - rho * ux * (cs2 + uy2);
-    const T n22 = R[2][2] - d * p.cs4 - rho * (cs2 * (ux2 + uy2) + ux2 * uy2);
-    const T N3 = n20 + n02, N4 = n20 - n02;
+    const V ux2 = vmul(ux, ux), uy2 = vmul(uy, uy);
+    const V nd = vneg(d), nrho = vneg(rho);
+    const V n20 = vfma(nrho, ux2, vfma(nd, c.cs2, R[2][0]));
+    const V n02 = vfma(nrho, uy2, vfma(nd, c.cs2, R[0][2]));
+    const V n11 = vfma(vmul(nrho, ux), uy, R[1][1]);
+    const V n21 = vfma(vmul(nrho, uy), vadd(c.cs2, ux2), R[2][1]);
+    const V n12 = vfma(vmul(nrho, ux), vadd(c.cs2, uy2), R[1][2]);
+    const V n22 = vfma(nrho, vfma(c.cs2, vadd(ux2, uy2), vmul(ux2, uy2)),
+                       vfma(nd, c.cs4, R[2][2]));
+    const V N3 = vadd(n20, n02), N4 = vsub(n20, n02);
 
     // Local strain rates, Eq. 37-38, and corrections, Eq. 23-26.
-    const T b1 = p.b1c + T(1.5) * ux2, b2 = p.b2c + T(1.5) * uy2;
-    const T c1 = p.c1c + T(1.5) * ux2, c2 = p.c2c - T(1.5) * uy2;
-    const T gx = p.g1h * ux * dxr, gy = p.g2h * uy * dyr;
-    const T R3 = N3 + gx + gy;
-    const T R4 = N4 + gx - gy;
-    const T idet = rcp(rho * (b1 * c2 - b2 * c1));
-    const T dxux = (c2 * R3 - b2 * R4) * idet;
-    const T dyuy = (b1 * R4 - c1 * R3) * idet;
-    const T Px = p.g1i * (rho * dxux + ux * dxr) - p.g3 * rho * ux2 * dxux;
-    const T Py = p.g2i * (rho * dyuy + uy * dyr) - p.g3 * rho * uy2 * dyuy;
+    const V b1 = vfma(c.c15, ux2, c.b1c), b2 = vfma(c.c15, uy2, c.b2c);
+    const V c1 = vfma(c.c15, ux2, c.c1c), c2 = vfma(c.nc15, uy2, c.c2c);
+    const V gx = vmul(vmul(c.g1h, ux), dxr), gy = vmul(vmul(c.g2h, uy), dyr);
+    const V R3 = vadd(vadd(N3, gx), gy);
+    const V R4 = vsub(vadd(N4, gx), gy);
+    const V idet = vrcp(vmul(rho, vfma(b1, c2, vmul(vneg(b2), c1))));
+    const V dxux = vmul(vfma(c2, R3, vmul(vneg(b2), R4)), idet);
+    const V dyuy = vmul(vfma(b1, R4, vmul(vneg(c1), R3)), idet);
+    const V rdx = vmul(rho, dxux), rdy = vmul(rho, dyuy);
+    const V Px = vfma(c.g1i, vfma(ux, dxr, rdx), vmul(vmul(c.ng3, rdx), ux2));
+    const V Py = vfma(c.g2i, vfma(uy, dyr, rdy), vmul(vmul(c.ng3, rdy), uy2));
 
     // Relaxation with the raw source moments of Eq. 13: increments of the
     // raw moments.  m1 relaxes to rho ux = m1 + Fx/2, so its increment is Fx
     // whatever omega_1 (same for m2).
-    const T Fx = p.Fx, Fy = p.Fy;
-    const T dm3 = p.lw3 * (Px + Py + T(2) * (Fx * ux + Fy * uy)) - p.w3 * N3;
-    const T dm4 = p.lw4 * (Px - Py + T(2) * (Fx * ux - Fy * uy)) - p.w4 * N4;
-    const T D20 = T(0.5) * (dm3 + dm4), D02 = T(0.5) * (dm3 - dm4);
-    const T D11 = p.lw5 * (Fx * uy + Fy * ux) - p.w5 * n11;
-    const T D21 = p.lw6 * (Fy * ux2 + T(2) * Fx * ux * uy) - p.w6 * n21;
-    const T D12 = p.lw7 * (Fx * uy2 + T(2) * Fy * ux * uy) - p.w7 * n12;
-    const T D22 = p.lw8 * T(2) * (Fx * ux * uy2 + Fy * uy * ux2) - p.w8 * n22;
+    const V uFx = vmul(ux, c.Fx), uFy = vmul(uy, c.Fy);
+    const V dm3 = vfma(c.lw3, vfma(c.two, vadd(uFx, uFy), vadd(Px, Py)), vmul(c.nw3, N3));
+    const V dm4 = vfma(c.lw4, vfma(c.two, vsub(uFx, uFy), vsub(Px, Py)), vmul(c.nw4, N4));
+    const V D20 = vmul(c.half, vadd(dm3, dm4)), D02 = vmul(c.half, vsub(dm3, dm4));
+    const V D11 = vfma(c.lw5, vfma(c.Fx, uy, vmul(c.Fy, ux)), vmul(c.nw5, n11));
+    const V D21 = vfma(c.lw6, vfma(c.Fy, ux2, vmul(vmul(c.twoFx, ux), uy)), vmul(c.nw6, n21));
+    const V D12 = vfma(c.lw7, vfma(c.Fx, uy2, vmul(vmul(c.twoFy, ux), uy)), vmul(c.nw7, n12));
+    const V D22 = vfma(c.lw8, vmul(c.two, vfma(uFx, uy2, vmul(uFy, ux2))), vmul(c.nw8, n22));
 
     // Back along x (raw x-moments -> columns), then along y.
-    T h[3][3];
-    {
-        const T Dq0[3] = {T(0), Fx, D20};
-        const T Dq1[3] = {Fy, D11, D21};
-        const T Dq2[3] = {D02, D12, D22};
-        const T* Dq[3] = {Dq0, Dq1, Dq2};
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            h[0][q] = Dq[q][0] - Dq[q][2];
-            h[1][q] = T(0.5) * (Dq[q][2] + Dq[q][1]);
-            h[2][q] = T(0.5) * (Dq[q][2] - Dq[q][1]);
-        }
-    }
+    V h[3][3];
+    h[0][0] = vneg(D20);
+    h[1][0] = vmul(c.half, vadd(D20, c.Fx));
+    h[2][0] = vmul(c.half, vsub(D20, c.Fx));
+    h[0][1] = vsub(c.Fy, D21);
+    h[1][1] = vmul(c.half, vadd(D21, D11));
+    h[2][1] = vmul(c.half, vsub(D21, D11));
+    h[0][2] = vsub(D02, D22);
+    h[1][2] = vmul(c.half, vadd(D22, D12));
+    h[2][2] = vmul(c.half, vsub(D22, D12));
     {
         const int iz[3] = {0, 1, 3}, ip[3] = {2, 5, 6}, im[3] = {4, 8, 7};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const T t2 = p.iah2 * h[c][2], t1 = p.iah * h[c][1];
-            f[iz[c]] += h[c][0] - p.ia2 * h[c][2];
-            f[ip[c]] += t2 + t1;
-            f[im[c]] += t2 - t1;
+        for (int X = 0; X < 3; ++X) {
+            f[iz[X]] = vadd(f[iz[X]], vfma(c.nia2, h[X][2], h[X][0]));
+            f[ip[X]] = vfma(c.iah2, h[X][2], vfma(c.iah, h[X][1], f[ip[X]]));
+            f[im[X]] = vfma(c.iah2, h[X][2], vfma(c.niah, h[X][1], f[im[X]]));
         }
     }
     return rho;

@@ -412,29 +412,65 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
             ldv<T, VC>(ring + sN * RW + c0 + 4, dNv);
             ldv<T, VC>(ring + sS * RW + c0 + 4, dSv);
             const bool edge_row = rc == 0 || rc == p.ny - 1;
+            // density gradient by central differences; a wall or solid
+            // neighbour mirrors the cell's own density
+            T dxr[VC], dyr[VC], rho[VC];
 #pragma unroll
             for (int j = 0; j < VC; ++j) {
                 const unsigned b = sbp[j];
-                T f[9];
+                const T d = dp[j];
+                const T dW = (b & 1u) ? d : dCv[j];
+                const T dS = (b & 2u) ? d : dSv[j];
+                const T dE = (b & 4u) ? d : dCv[j + 2];
+                const T dN = (b & 8u) ? d : dNv[j];
+                dxr[j] = T(0.5) * (dE - dW);
+                dyr[j] = p.iah * (dN - dS);
+                rho[j] = p.rho0 + d;
+            }
+            if (p.collide) {
+                if constexpr (sizeof(T) == 4) {
+                    // both cells in one float2 lane pair
+                    static_assert(VC == 2, "FP32 collides its two cells as one float2");
+                    float2 F[9];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) f[i] = g[i][j];
-                if (b != 0xFFu) {
-                    const T d = dp[j];
-                    const T dW = (b & 1u) ? d : dCv[j];
-                    const T dS = (b & 2u) ? d : dSv[j];
-                    const T dE = (b & 4u) ? d : dCv[j + 2];
-                    const T dN = (b & 8u) ? d : dNv[j];
-                    const T dxr = T(0.5) * (dE - dW);
-                    const T dyr = p.iah * (dN - dS);
-                    const T rho = !p.collide ? p.rho0 + d
-                                  : p.raw  ? collide_raw(p, f, d, dxr, dyr)
-                                           : collide(p, f, d, dxr, dyr);
-                    const int cx = xa + j;
-                    if (p.moving && (cx == 0 || cx == p.nx - 1 || edge_row))
-                        moving_wall(p, cx, rc, rho, f);
+                    for (int i = 0; i < 9; ++i) F[i] = make_float2(g[i][0], g[i][1]);
+                    const float2 D = make_float2(dp[0], dp[1]);
+                    const float2 Gx = make_float2(dxr[0], dxr[1]), Gy = make_float2(dyr[0], dyr[1]);
+                    const float2 R = p.raw ? collide_raw<float>(p.cc, F, D, Gx, Gy)
+                                           : collide<float>(p.cc, F, D, Gx, Gy);
+                    rho[0] = R.x;
+                    rho[1] = R.y;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        if (sbp[0] != 0xFFu) g[i][0] = F[i].x;
+                        if (sbp[1] != 0xFFu) g[i][1] = F[i].y;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < VC; ++j) {
+                        if (sbp[j] == 0xFFu) continue;
+                        T F[9];
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) F[i] = g[i][j];
+                        rho[j] = p.raw ? collide_raw<T>(p.cc, F, dp[j], dxr[j], dyr[j])
+                                       : collide<T>(p.cc, F, dp[j], dxr[j], dyr[j]);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) g[i][j] = F[i];
+                    }
                 }
+            }
+            if (p.moving) {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) g[i][j] = f[i];
+                for (int j = 0; j < VC; ++j) {
+                    const int cx = xa + j;
+                    if (sbp[j] == 0xFFu || !(cx == 0 || cx == p.nx - 1 || edge_row)) continue;
+                    T f[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i] = g[i][j];
+                    moving_wall(p, cx, rc, rho[j], f);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i][j] = f[i];
+                }
             }
             const I o = (I)rc * rs + xa;
 #pragma unroll
