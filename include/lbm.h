@@ -227,7 +227,8 @@ const char* lbm_last_error(const lbm_handle* h);
  *
  * Every step of a batch is one launch of a persistent kernel that walks a
  * device work list of (lattice, column segment, band of rows) items of the
- * active lattices; runs of 50 steps replay a captured CUDA graph.  Lattices
+ * active lattices (two launches when the batch mixes the RC-LBM and RNR-LBM
+ * schemes, one per scheme); runs of 50 steps replay a captured CUDA graph.  Lattices
  * can be retired (made inactive) and brought back; an inactive lattice keeps
  * its state and is not stepped.  Conventions as for lbm_handle; work is
  * issued on the stream given to lbm_batch_create.
@@ -315,7 +316,8 @@ lbm_status lbm_batch_diagnostics(lbm_batch* b, int k, double out[LBM_DIAG_COUNT]
 /* Steps taken by lattice k since its last init (-1 for a bad argument). */
 int64_t lbm_batch_step_count(const lbm_batch* b, int k);
 
-/* Batch step kernel launches issued so far (one per step). */
+/* Batch step kernel launches issued so far: one per step, two when the
+ * batch holds lattices of both schemes (one persistent launch each). */
 int64_t lbm_batch_launch_count(const lbm_batch* b);
 
 /* Message of the last error on b (or of the last failed lbm_batch_create

@@ -868,9 +868,13 @@ struct lbm_batch {
     double* ubase = nullptr;
     BatchLattice<float>* d_lat = nullptr;
     BatchAux* d_aux = nullptr;
-    int* d_list = nullptr;  // active[count] begin[count] rbegin[count] counts[2] rcounts[2]
+    // work lists, each {lattice[count], first item[count], counts[2]}: one
+    // per scheme for the step (0: RC-LBM or no collision, 1: RNR-LBM), one
+    // of all active lattices for the residual
+    int* d_list = nullptr;
     std::vector<int> h_list;
-    int n_active = 0, total_items = 0, total_chunks = 0;
+    bool has_scheme[2] = {false, false};
+    int n_active = 0, total_chunks = 0;
     bool list_dirty = true;
     ResPartial* d_part = nullptr;  // per reduction block
     ResPartial* d_res = nullptr;   // per lattice
@@ -941,47 +945,61 @@ lbm_status set_shape(lbm_batch* b, int bx, int rows) {
     return LBM_OK;
 }
 
+// Offset of work list w (0, 1: step lists of the schemes; 2: residual list)
+// in d_list / h_list.
+size_t list_at(const lbm_batch* b, int w) { return (size_t)w * (2 * (size_t)b->count + 2); }
+
 // Uploads the work lists of the active lattices (if they changed).
 lbm_status upload_list(lbm_batch* b) {
     if (!b->list_dirty) return LBM_OK;
     const int C = b->count;
-    int n = 0;
-    long long items = 0, chunks = 0;
+    int n[3] = {0, 0, 0};
+    long long items[3] = {0, 0, 0};
     for (int k = 0; k < C; ++k) {
         if (!b->active[k]) continue;
-        b->h_list[n] = k;
-        b->h_list[C + n] = (int)items;
-        b->h_list[2 * C + n] = (int)chunks;
-        items += (long long)b->lat[k].nseg * b->lat[k].nbands;
-        chunks += b->bax[k].nchunk;
-        ++n;
+        const int w = b->p[k].scheme == 1 ? 1 : 0;
+        int* Lw = b->h_list.data() + list_at(b, w);
+        Lw[n[w]] = k;
+        Lw[C + n[w]] = (int)items[w];
+        items[w] += (long long)b->lat[k].nseg * b->lat[k].nbands;
+        ++n[w];
+        int* Lr = b->h_list.data() + list_at(b, 2);
+        Lr[n[2]] = k;
+        Lr[C + n[2]] = (int)items[2];
+        items[2] += b->bax[k].nchunk;
+        ++n[2];
     }
-    if (items > (1LL << 30) || chunks > (1LL << 30)) {
-        bset_err(b, "the batch's work list is too long");
-        return LBM_ERR_INVALID;
+    for (int w = 0; w < 3; ++w) {
+        if (items[w] > (1LL << 30)) {
+            bset_err(b, "the batch's work list is too long");
+            return LBM_ERR_INVALID;
+        }
+        int* Lw = b->h_list.data() + list_at(b, w);
+        Lw[2 * C] = n[w];
+        Lw[2 * C + 1] = (int)items[w];
     }
-    b->h_list[3 * C] = n;
-    b->h_list[3 * C + 1] = (int)items;
-    b->h_list[3 * C + 2] = n;
-    b->h_list[3 * C + 3] = (int)chunks;
-    BCK(b, cudaMemcpyAsync(b->d_list, b->h_list.data(), sizeof(int) * (3 * C + 4),
+    BCK(b, cudaMemcpyAsync(b->d_list, b->h_list.data(), sizeof(int) * b->h_list.size(),
                            cudaMemcpyHostToDevice, b->stream),
         "cudaMemcpyAsync(work list)");
-    b->n_active = n;
-    b->total_items = (int)items;
-    b->total_chunks = (int)chunks;
+    b->n_active = n[2];
+    b->total_chunks = (int)items[2];
     b->list_dirty = false;
     return LBM_OK;
 }
 
+int kernels_per_step(const lbm_batch* b) { return (int)b->has_scheme[0] + (int)b->has_scheme[1]; }
+
 cudaError_t launch_steps(lbm_batch* b, int n, int parity, cudaStream_t s) {
     const int C = b->count;
-    for (int i = 0; i < n; ++i) {
-        cudaError_t e = lbm::launch_batch_step<float>(b->d_lat, b->d_list, b->d_list + C,
-                                                      b->d_list + 3 * C, (parity + i) & 1,
-                                                      b->bx, b->grid, s);
-        if (e != cudaSuccess) return e;
-    }
+    for (int i = 0; i < n; ++i)
+        for (int w = 0; w < 2; ++w) {
+            if (!b->has_scheme[w]) continue;
+            const int* Lw = b->d_list + list_at(b, w);
+            cudaError_t e = lbm::launch_batch_step<float>(b->d_lat, Lw, Lw + C, Lw + 2 * C,
+                                                          (parity + i) & 1, b->bx, b->grid, w,
+                                                          s);
+            if (e != cudaSuccess) return e;
+        }
     return cudaSuccess;
 }
 
@@ -1097,7 +1115,7 @@ lbm_status lbm_batch_create(const lbm_params* params, int count,
     b->steps.assign(count, 0);
     b->prev_step.assign(count, 0);
     b->last_res.assign(count, -1.0);
-    b->h_list.assign(3 * (size_t)count + 4, 0);
+    b->h_list.assign(3 * (2 * (size_t)count + 2), 0);
     b->h_res.resize(count);
 
     // one allocation each for the populations (two buffers per lattice), the
@@ -1141,7 +1159,8 @@ lbm_status lbm_batch_create(const lbm_params* params, int count,
     BCKC(cudaMemsetAsync(b->status, 0, sizeof(int), b->stream), "cudaMemset");
     BCKC(cudaMalloc(&b->d_lat, sizeof(BatchLattice<float>) * count), "cudaMalloc(lattice table)");
     BCKC(cudaMalloc(&b->d_aux, sizeof(BatchAux) * count), "cudaMalloc(lattice table)");
-    BCKC(cudaMalloc(&b->d_list, sizeof(int) * (3 * (size_t)count + 4)), "cudaMalloc(work list)");
+    BCKC(cudaMalloc(&b->d_list, sizeof(int) * b->h_list.size()), "cudaMalloc(work list)");
+    for (int k = 0; k < count; ++k) b->has_scheme[params[k].scheme == 1 ? 1 : 0] = true;
     BCKC(cudaMalloc(&b->d_part, sizeof(ResPartial) * (size_t)chunks), "cudaMalloc(residual sums)");
     BCKC(cudaMalloc(&b->d_res, sizeof(ResPartial) * (size_t)count), "cudaMalloc(residual sums)");
     b->diag_blocks = 2 * b->sms;
@@ -1273,13 +1292,13 @@ lbm_status advance(lbm_batch* b, int64_t nsteps, bool graphs) {
         if (lbm_status s = ensure_graph(b, b->parity); s != LBM_OK) return s;
         BCK(b, cudaGraphLaunch(b->graph[b->parity], b->stream), "cudaGraphLaunch");
         left -= kGraphSteps;
-        b->launches += kGraphSteps;
+        b->launches += kGraphSteps * kernels_per_step(b);
     }
     while (left > 0) {
         const int n = left < (1 << 20) ? (int)left : (1 << 20);
         BCK(b, launch_steps(b, n, (int)((b->parity + (nsteps - left)) & 1), b->stream),
             "batch step kernel");
-        b->launches += n;
+        b->launches += n * kernels_per_step(b);
         left -= n;
     }
     b->parity = (int)((b->parity + nsteps) & 1);
@@ -1309,9 +1328,10 @@ lbm_status lbm_batch_residuals(lbm_batch* b, double* res) {
     const int C = b->count;
     int kstatus = 0;
     if (b->n_active > 0) {
-        BCK(b, lbm::launch_batch_residual(b->d_lat, b->d_aux, b->d_list, b->d_list + 2 * C,
-                                          b->d_list + 3 * C + 2, b->parity, b->d_part, b->d_res,
-                                          b->n_active, b->total_chunks, b->stream),
+        const int* Lr = b->d_list + list_at(b, 2);
+        BCK(b, lbm::launch_batch_residual(b->d_lat, b->d_aux, Lr, Lr + C, Lr + 2 * C, b->parity,
+                                          b->d_part, b->d_res, b->n_active, b->total_chunks,
+                                          b->stream),
             "batch residual kernels");
         BCK(b, cudaMemcpyAsync(b->h_res.data(), b->d_res, sizeof(ResPartial) * C,
                                cudaMemcpyDeviceToHost, b->stream),

@@ -20,6 +20,11 @@ struct DiagPartial {
 template <typename T>
 cudaError_t launch_step(const T* fin, T* fout, const KParams<T>& p, int bx, int nbands,
                         cudaStream_t s);
+// the same with the raw-moment collision (RNR-LBM); launch_step calls it
+// when p.raw is set
+template <typename T>
+cudaError_t launch_step_rnr(const T* fin, T* fout, const KParams<T>& p, int bx, int nbands,
+                            cudaStream_t s);
 template <typename T>
 int step_occupancy(int bx, bool mask);
 // columns of lattice one block of bx threads of the step kernel covers
@@ -33,11 +38,13 @@ struct BatchLattice {
     T* f[2];              // its two population buffers
     int nseg, nbands;     // its work items: nseg * nbands blocks
 };
-// One step of every active lattice of a batch: counts = {number of active
-// lattices, total work items}, begin[k] = first work item of active[k].
+// One step of every lattice of a work list (all of one scheme: raw = 1 for
+// RNR-LBM, else RC-LBM or no collision): counts = {number of lattices, total
+// work items}, begin[k] = first work item of active[k].
 template <typename T>
 cudaError_t launch_batch_step(const BatchLattice<T>* lat, const int* active, const int* begin,
-                              const int* counts, int parity, int bx, int grid, cudaStream_t s);
+                              const int* counts, int parity, int bx, int grid, int raw,
+                              cudaStream_t s);
 template <typename T>
 int batch_occupancy(int bx);
 

@@ -51,7 +51,8 @@ def test_transient_couette_a01(precision):
 def test_womersley_a0125(precision):
     """Sec. 5.3: oscillating body force F_m cos(w t) between two plates,
     H = 50 over 400 cells (a = 0.125), T = 40,000, Wo = 4.25, tau = 1,
-    F_m = 1e-5; three periods, then u(y) at eight phases of the last one."""
+    F_m = 1e-5; from the periodic solution at t = 0, u(y) at eight phases
+    of the third period."""
     a, ny, nx = 0.125, 400, 4
     H, T, Wo, tau, Fm = ny * a, 40000, 4.25, 1.0, 1e-5
     w = 2 * np.pi / T
@@ -59,11 +60,14 @@ def test_womersley_a0125(precision):
     cs2 = nu / (tau - 0.5)
     wl = W.Workload("womersley", nx, ny, a, cs2, W.omega_for(nu, cs2), periodic_x=1,
                     periodic_y=0)
-    g = lattice(wl, precision)
     yc = (np.arange(ny) + 0.5) * a - H / 2
     k = np.sqrt(1j * w / nu)
     shape = 1 - np.cosh(k * yc) / np.cosh(k * H / 2)
     amp = np.abs(Fm / (1j * w) * shape).max()
+    # start on the periodic solution at t = 0: a start from rest would carry
+    # a transient that decays only over H^2 / (pi^2 nu) ~ 47,000 steps
+    u0 = np.real(Fm / (1j * w) * shape)[:, None] * np.ones((1, nx))
+    g = lattice(wl.with_(rho=np.ones((ny, nx)), ux=u0, uy=np.zeros((ny, nx))), precision)
     checks = set(2 * T + T * np.arange(8) // 8)
     worst = 0.0
     for n in range(3 * T):
@@ -101,4 +105,5 @@ def test_shallow_cavity_square_vs_rectangular():
     v_rc = vr[62, :] / U
     x_sq = (np.arange(400) + 0.5) / 400
     x_rc = (np.arange(100) + 0.5) / 100
-    assert np.abs(np.interp(x_sq, x_rc, v_rc) - v_sq).max() < 0.02
+    inside = (x_sq >= x_rc[0]) & (x_sq <= x_rc[-1])   # no extrapolation
+    assert np.abs(np.interp(x_sq, x_rc, v_rc) - v_sq)[inside].max() < 0.02
