@@ -1,0 +1,128 @@
+"""Pins of the FP64 reference of the warm-start surrogate network.
+
+The hand-written backward pass against central finite differences, the
+convolution against its definition evaluated cell by cell, the pooling and
+upsampling against their adjoints, the bfloat16 rounding against PyTorch's
+conversion, and the first Adam step against its closed form.
+"""
+import numpy as np
+import pytest
+
+from oracle import surrogate_oracle as S
+
+
+def test_conv3x3_matches_its_definition_cell_by_cell():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((2, 5, 4, 3))
+    w = rng.standard_normal((3, 3, 3, 2))
+    b = rng.standard_normal(2)
+    y = S.conv3x3(x, w, b)
+    for n in range(2):
+        for i in range(5):
+            for j in range(4):
+                for o in range(2):
+                    s = b[o]
+                    for dy in range(3):
+                        for dx in range(3):
+                            yy, xx = i + dy - 1, j + dx - 1
+                            if 0 <= yy < 5 and 0 <= xx < 4:
+                                s += sum(x[n, yy, xx, c] * w[dy, dx, c, o] for c in range(3))
+                    assert abs(y[n, i, j, o] - s) < 1e-12
+
+
+def test_pool_and_upsample_backward_are_adjoints():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 6, 8, 3))
+    y = rng.standard_normal((2, 3, 4, 3))
+    assert np.isclose((S.avgpool2(x) * y).sum(), (x * S.avgpool2_backward(y)).sum(), rtol=1e-13)
+    z = rng.standard_normal((2, 6, 8, 3))
+    assert np.isclose((S.upsample2(y) * z).sum(), (y * S.upsample2_backward(z)).sum(), rtol=1e-13)
+
+
+def test_conv_backward_is_the_adjoint():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((1, 4, 6, 3))
+    w = rng.standard_normal((3, 3, 3, 5))
+    gy = rng.standard_normal((1, 4, 6, 5))
+    gx, gw, gb = S.conv3x3_backward(x, w, gy)
+    # <conv(x, w, 0), gy> is linear in x and in w
+    lin = (S.conv3x3(x, w, np.zeros(5)) * gy).sum()
+    assert np.isclose((gx * x).sum(), lin, rtol=1e-12)
+    assert np.isclose((gw * w).sum(), lin, rtol=1e-12)
+    assert np.allclose(gb, gy.sum(axis=(0, 1, 2)))
+
+
+@pytest.mark.parametrize("channels", [[4, 8], [3, 5, 6]])
+def test_backward_matches_finite_differences(channels):
+    params = S.init_params(channels, seed=3)
+    net = S.WarmNet(channels, params)
+    rng = np.random.default_rng(4)
+    hw = 2 ** (len(channels) + 1)
+    x = rng.standard_normal((2, hw, hw, 4))
+    t = rng.standard_normal((2, hw, hw, 3))
+    fluid = rng.random((2, hw, hw)) > 0.2
+    y, tape = net.forward(x)
+    _, gy = net.loss(y, t, fluid)
+    grads = net.backward(tape, gy)
+    eps = 1e-6
+    for k, (w, b) in enumerate(net.params):
+        for idx in [(0, 0, 0, 0), (1, 2, w.shape[2] - 1, w.shape[3] // 2), (2, 1, 0, w.shape[3] - 1)]:
+            w[idx] += eps
+            lp = net.loss(net.forward(x)[0], t, fluid)[0]
+            w[idx] -= 2 * eps
+            lm = net.loss(net.forward(x)[0], t, fluid)[0]
+            w[idx] += eps
+            fd = (lp - lm) / (2 * eps)
+            assert abs(grads[k][0][idx] - fd) <= 1e-6 * max(1e-3, abs(fd)), (k, idx)
+        j = b.shape[0] - 1
+        b[j] += eps
+        lp = net.loss(net.forward(x)[0], t, fluid)[0]
+        b[j] -= 2 * eps
+        lm = net.loss(net.forward(x)[0], t, fluid)[0]
+        b[j] += eps
+        fd = (lp - lm) / (2 * eps)
+        assert abs(grads[k][1][j] - fd) <= 1e-6 * max(1e-3, abs(fd)), (k, "bias")
+
+
+def test_solid_cells_do_not_count_in_the_loss():
+    channels = [4, 8]
+    net = S.WarmNet(channels, S.init_params(channels, seed=5))
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((1, 8, 8, 4))
+    y, _ = net.forward(x)
+    t = y.copy()
+    fluid = np.ones((1, 8, 8), bool)
+    fluid[0, 2, 3] = False
+    t[0, 2, 3] += 5.0
+    loss, g = net.loss(y, t, fluid)
+    assert loss == 0.0 and np.all(g == 0.0)
+
+
+def test_config_network_shapes():
+    channels = [32, 64, 128, 256]
+    shapes = S.layer_shapes(channels)
+    assert len(shapes) == 15 and shapes[0] == (4, 32) and shapes[-1] == (32, 3)
+    net = S.WarmNet(channels, S.init_params(channels, seed=7))
+    y, _ = net.forward(np.zeros((1, 16, 16, 4)))
+    assert y.shape == (1, 16, 16, 3)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    v = np.concatenate([rng.standard_normal(10000) * 10.0 ** rng.integers(-6, 6, 10000),
+                        [1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -2.5, 0.0]])
+    v32 = v.astype(np.float32)
+    ref = torch.from_numpy(v32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(S.bf16(v32), ref)
+    assert S.bf16(1.0 + 2.0 ** -8) == 1.0          # tie to even
+    assert S.bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+
+
+def test_first_adam_step_closed_form():
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    q, m, v = S.adam_step(p, g, np.zeros(3), np.zeros(3), 1, lr=1e-2, eps=1e-8)
+    # first step: m_hat = g, v_hat = g^2, so the update is lr g / (|g| + eps)
+    assert np.allclose(q, p - 1e-2 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
