@@ -132,10 +132,12 @@ __device__ __forceinline__ void stv(T* p, const T* in) {
 template <typename T>
 __host__ __device__ constexpr int step_cells_per_thread() { return 2; }
 
+// mbarriers, the population stages, the density ring and the link-mask stages
 template <typename T, int BXT>
 constexpr size_t step_smem_bytes() {
     constexpr int W = BXT * step_cells_per_thread<T>();
-    return 128 + (size_t)kStages * 9 * (W + 2 * kHalo) * sizeof(T) + 4 * (W + 8) * sizeof(T);
+    return 128 + (size_t)kStages * 9 * (W + 2 * kHalo) * sizeof(T) + 4 * (W + 8) * sizeof(T) +
+           (size_t)kStages * W;
 }
 
 // I: element-offset type, int while 9 * plane < 2^31, else long long.
@@ -159,6 +161,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem);
     T* stage = reinterpret_cast<T*>(smem + 128);        // [kStages][9][SW]
     T* ring = stage + kStages * 9 * SW;                 // [4][RW], column c at c - x0 + 4
+    const uint8_t* smask = reinterpret_cast<const uint8_t*>(ring + 4 * RW);  // [kStages][W]
 
     const int tx = threadIdx.x;
     const int lane = tx & 31;
@@ -215,11 +218,12 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         return Wb | (S << 1) | (Eb << 2) | (N << 3) | ((Wb | S) << 4) | ((Eb | S) << 5) |
                ((Eb | N) << 6) | ((Wb | N) << 7);
     };
-    // link bits of my VC cells in row rr; returns their OR (0: all fluid, no wall)
-    auto cell_bits = [&](int rr, unsigned* sb) -> unsigned {
+    // link bits of my VC cells in row rr (staged in stage s); returns their
+    // OR (0: all fluid, no wall)
+    auto cell_bits = [&](int s, int rr, unsigned* sb) -> unsigned {
         unsigned any = 0;
         if (MASK) {
-            const uint8_t* m = p.lmask + ((I)rr * pitch + xa);
+            const uint8_t* m = smask + s * W + c0;
 #pragma unroll
             for (int j = 0; j < VC; ++j) {
                 sb[j] = (c0 + j < nseg) ? (unsigned)m[j] : 0xFFu;
@@ -242,7 +246,11 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
 
     // warp 0: copies of the source rows of iteration k into its stage; lane 0
     // announces the byte count on the stage's mbarrier, lanes 0..8 copy one
-    // plane each
+    // plane each, lane 9 the row of the link mask (columns x0 .. x0 + mbytes;
+    // x0 and the row pitch are multiples of 32, so the copy is 16-byte
+    // aligned and stays inside the mask)
+    const unsigned mbytes = (unsigned)min(W, p.pitch - x0);
+    const unsigned sm0 = smem_u32(smask);
     auto issue = [&](int k) {
         const int s = k % kStages;
         const unsigned bar = bar0 + 8u * s;
@@ -261,11 +269,14 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
             if (sr >= 0) bytes += cbytes;
             if (i == lane) sr_mine = sr;
         }
+        if (MASK && ok) bytes += mbytes;
         if (lane == 0) mbar_expect_tx(bar, bytes);
         __syncwarp();
         if (lane < 9 && sr_mine >= 0)
             bulk_g2s(st0 + (unsigned)(((s * 9 + lane) * SW + dshift) * sizeof(T)),
                      fin + (lane * pl + (I)sr_mine * rs + wstart), cbytes, bar);
+        if (MASK && lane == 9 && ok)
+            bulk_g2s(sm0 + (unsigned)(s * W), p.lmask + ((I)rr * pitch + x0), mbytes, bar);
     };
 
     // populations g[i][j] of my VC cells (row rr) from stage s.  Fast: vector
@@ -345,7 +356,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
 #pragma unroll
         for (int j = 0; j < VC; ++j) { sbc[j] = 0xFFu; dc[j] = T(0); }
         if (!to && rv && any_active) {
-            const unsigned any = cell_bits(rr, sbc);
+            const unsigned any = cell_bits(s, rr, sbc);
             fastc = xfast && any == 0u;
             T g[9][VC];
             load(s, rr, sbc, fastc, g);
