@@ -22,10 +22,12 @@ computes out(y, x) = b + sum_{dy,dx} in(y + dy - 1, x + dx - 1) W[dy, dx]
 with zeros outside the grid.  avgpool2 averages 2x2 blocks; upsample2
 repeats each value into a 2x2 block.
 
-With ``bf16=True`` the weights and every stored activation are rounded to
-bfloat16 (round to nearest even) where the CUDA kernels store them, while
-sums stay in FP64; the loss, its gradient and all other gradients are not
-rounded.
+With ``bf16_storage=True`` the weights, every stored activation and every
+stored activation gradient are rounded to bfloat16 (round to nearest even)
+where the CUDA kernels store them -- the inputs, each layer's output, the
+loss gradient, each input gradient of a convolution, of an upsampling and
+of a pooling (together with the skip gradient it joins) -- while sums stay
+in FP64 and parameter gradients are not rounded.
 
 Loss: L = sum_m fluid(m) sum_c (y - t)^2 / (3 sum_m fluid(m)), over all
 cells m of the batch; solid cells do not count.
@@ -170,13 +172,14 @@ class WarmNet:
         The encoder output e_l of level l (l < L-1) feeds both the pool into
         level l+1 and the skip addition of decoder level l, so its gradient is
         the sum of the two; the addition passes its gradient to both inputs."""
+        r = self.rnd
         grads = [None] * len(self.params)
         skip_grads = {}
         pool_level = 0
         for item in tape:
             if item[0] == "pool":
                 pool_level += 1
-        g = gy
+        g = r(gy)
         for item in reversed(tape):
             if item[0] == "conv":
                 _, xin, k, relu, out = item
@@ -184,14 +187,14 @@ class WarmNet:
                     g = g * (out > 0.0)
                 gx, gw, gb = conv3x3_backward(xin, self.params[k][0], g)
                 grads[k] = (gw, gb)
-                g = gx
+                g = r(gx)
             elif item[0] == "skip":
                 skip_grads[item[1]] = g
             elif item[0] == "up":
-                g = upsample2_backward(g)
+                g = r(upsample2_backward(g))
             elif item[0] == "pool":
                 pool_level -= 1
-                g = avgpool2_backward(g) + skip_grads.pop(pool_level)
+                g = r(avgpool2_backward(g) + skip_grads.pop(pool_level))
         return grads
 
 

@@ -1,0 +1,1065 @@
+// nn.cu -- the warm-start surrogate of include/lbm_nn.h: a 3x3-convolution
+// encoder-decoder trained and evaluated on the GPU.
+//
+// The three GEMMs of a convolution run on the BF16 tensor cores
+// (mma.sync.m16n8k16, FP32 accumulation) as implicit GEMMs over NHWC
+// activations with channels padded to a multiple of 8:
+//   forward      M = pixels, N = cout, K = 9 cin:
+//                A[p][(tap, ci)] = in(p + s(tap))[ci], B[co][(tap, ci)] = W
+//   input grad   M = pixels, N = cin, K = 9 cout:
+//                A[q][(tap, co)] = g(q - s(tap))[co], B[ci][(tap, co)] = W
+//   weight grad  M = cout, N = 9 cin, K = pixels (split over blocks, the
+//                partial sums added in a fixed order):
+//                A[co][p] = g(p)[co], B[(tap, ci)][p] = in(p + s(tap))[ci]
+// with s(tap) = (dy - 1, dx - 1) and zeros outside the grid.  A block
+// computes a 64 x 64 tile with four warps (32 x 32 each) over K chunks of 32
+// staged in shared memory as [row][k] with a padded stride, from which each
+// thread reads its fragments with 32-bit loads.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <random>
+#include <vector>
+
+#include "lbm_nn.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int BM = 64, BN = 64, BK = 32, LDS = BK + 8;
+constexpr int kGemmThreads = 128;
+constexpr int kThreads = 256;
+constexpr int kSplitPixels = 4096;  // pixels per block of the weight-gradient GEMM
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+        "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+struct Geo {
+    int n, h, w;          // batch and grid
+    long long P;          // pixels n h w
+};
+
+__device__ __forceinline__ bool shifted(const Geo& g, long long p, int dy, int dx, long long& q) {
+    const int hw = g.h * g.w;
+    const int nn = (int)(p / hw);
+    const int rem = (int)(p - (long long)nn * hw);
+    const int y = rem / g.w + dy, x = rem % g.w + dx;
+    if (y < 0 || y >= g.h || x < 0 || x >= g.w) return false;
+    q = ((long long)nn * g.h + y) * g.w + x;
+    return true;
+}
+
+// Forward: out = act(conv(in) + b).
+struct FwdOp {
+    Geo g;
+    const bf16* in;    // [P][cin]
+    const bf16* wf;    // [cout][9 cin]
+    const float* bias; // [cout]
+    bf16* out;         // [P][cout]
+    int cin, cout, relu;
+    __host__ __device__ long long M() const { return g.P; }
+    __host__ __device__ int N() const { return cout; }
+    __host__ __device__ long long K() const { return 9LL * cin; }
+    __device__ void load_a(bf16* As, long long m0, long long k0, long long kend, int tid) const {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int v = tid + i * kGemmThreads, m = v >> 2, kq = (v & 3) * 8;
+            const long long p = m0 + m, k = k0 + kq;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (p < g.P && k < kend) {
+                const int tap = (int)(k / cin), ci = (int)(k - (long long)tap * cin);
+                long long q;
+                if (shifted(g, p, tap / 3 - 1, tap % 3 - 1, q))
+                    val = *reinterpret_cast<const uint4*>(in + q * cin + ci);
+            }
+            *reinterpret_cast<uint4*>(As + m * LDS + kq) = val;
+        }
+    }
+    __device__ void load_b(bf16* Bs, int n0, long long k0, long long kend, int tid) const {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int v = tid + i * kGemmThreads, nn = v >> 2, kq = (v & 3) * 8;
+            const long long k = k0 + kq;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (n0 + nn < cout && k < kend)
+                val = *reinterpret_cast<const uint4*>(wf + (long long)(n0 + nn) * K() + k);
+            *reinterpret_cast<uint4*>(Bs + nn * LDS + kq) = val;
+        }
+    }
+    __device__ void store(long long row, int col, float v0, float v1, int) const {
+        if (row >= g.P || col >= cout) return;
+        v0 += bias[col];
+        v1 += bias[col + 1];
+        if (relu) {
+            v0 = fmaxf(v0, 0.0f);
+            v1 = fmaxf(v1, 0.0f);
+        }
+        *reinterpret_cast<__nv_bfloat162*>(out + row * cout + col) = __floats2bfloat162_rn(v0, v1);
+    }
+};
+
+// Input gradient: gin = conv^T(gpre).
+struct DgradOp {
+    Geo g;
+    const bf16* gpre;  // [P][cout]
+    const bf16* wd;    // [cin][9 cout]
+    bf16* gin;         // [P][cin]
+    int cin, cout;
+    __host__ __device__ long long M() const { return g.P; }
+    __host__ __device__ int N() const { return cin; }
+    __host__ __device__ long long K() const { return 9LL * cout; }
+    __device__ void load_a(bf16* As, long long m0, long long k0, long long kend, int tid) const {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int v = tid + i * kGemmThreads, m = v >> 2, kq = (v & 3) * 8;
+            const long long p = m0 + m, k = k0 + kq;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (p < g.P && k < kend) {
+                const int tap = (int)(k / cout), co = (int)(k - (long long)tap * cout);
+                long long q;
+                if (shifted(g, p, 1 - tap / 3, 1 - tap % 3, q))
+                    val = *reinterpret_cast<const uint4*>(gpre + q * cout + co);
+            }
+            *reinterpret_cast<uint4*>(As + m * LDS + kq) = val;
+        }
+    }
+    __device__ void load_b(bf16* Bs, int n0, long long k0, long long kend, int tid) const {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int v = tid + i * kGemmThreads, nn = v >> 2, kq = (v & 3) * 8;
+            const long long k = k0 + kq;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (n0 + nn < cin && k < kend)
+                val = *reinterpret_cast<const uint4*>(wd + (long long)(n0 + nn) * K() + k);
+            *reinterpret_cast<uint4*>(Bs + nn * LDS + kq) = val;
+        }
+    }
+    __device__ void store(long long row, int col, float v0, float v1, int) const {
+        if (row >= g.P || col >= cin) return;
+        *reinterpret_cast<__nv_bfloat162*>(gin + row * cin + col) = __floats2bfloat162_rn(v0, v1);
+    }
+};
+
+// Weight gradient, one split of the pixels per blockIdx.z: part[z][co][(tap, ci)].
+struct WgradOp {
+    Geo g;
+    const bf16* gpre;  // [P][cout]
+    const bf16* in;    // [P][cin]
+    float* part;       // [splits][cout][9 cin]
+    int cin, cout;
+    __host__ __device__ long long M() const { return cout; }
+    __host__ __device__ int N() const { return 9 * cin; }
+    __host__ __device__ long long K() const { return g.P; }
+    __device__ void load_a(bf16* As, long long m0, long long k0, long long kend, int tid) const {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int v = tid + i * kGemmThreads, kk = v >> 3, c8 = (v & 7) * 8;
+            const long long p = k0 + kk;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (p < kend && m0 + c8 < cout)
+                val = *reinterpret_cast<const uint4*>(gpre + p * cout + m0 + c8);
+            const bf16* e = reinterpret_cast<const bf16*>(&val);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) As[(c8 + j) * LDS + kk] = e[j];
+        }
+    }
+    __device__ void load_b(bf16* Bs, int n0, long long k0, long long kend, int tid) const {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int v = tid + i * kGemmThreads, kk = v >> 3, c8 = (v & 7) * 8;
+            const long long p = k0 + kk;
+            const int n = n0 + c8;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (p < kend && n < N()) {
+                const int tap = n / cin, ci = n - tap * cin;
+                long long q;
+                if (shifted(g, p, tap / 3 - 1, tap % 3 - 1, q))
+                    val = *reinterpret_cast<const uint4*>(in + q * cin + ci);
+            }
+            const bf16* e = reinterpret_cast<const bf16*>(&val);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) Bs[(c8 + j) * LDS + kk] = e[j];
+        }
+    }
+    __device__ void store(long long row, int col, float v0, float v1, int z) const {
+        if (row >= cout || col >= N()) return;
+        float* d = part + ((long long)z * cout + row) * N() + col;
+        d[0] = v0;
+        d[1] = v1;
+    }
+};
+
+template <class Op>
+__global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const Op op, long long kchunk) {
+    __shared__ __align__(16) bf16 As[BM * LDS];
+    __shared__ __align__(16) bf16 Bs[BN * LDS];
+    const long long m0 = (long long)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const long long kbeg = (long long)blockIdx.z * kchunk;
+    const long long kend = min(op.K(), kbeg + kchunk);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int gq = lane >> 2, t = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
+    for (long long k0 = kbeg; k0 < kend; k0 += BK) {
+        op.load_a(As, m0, k0, kend, tid);
+        op.load_b(Bs, n0, k0, kend, tid);
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t a[2][4], b[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                const bf16* base = As + (wm + mi * 16 + gq) * LDS + kk + 2 * t;
+                a[mi][0] = *reinterpret_cast<const uint32_t*>(base);
+                a[mi][1] = *reinterpret_cast<const uint32_t*>(base + 8 * LDS);
+                a[mi][2] = *reinterpret_cast<const uint32_t*>(base + 8);
+                a[mi][3] = *reinterpret_cast<const uint32_t*>(base + 8 * LDS + 8);
+            }
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                const bf16* bb = Bs + (wn + ni * 8 + gq) * LDS + kk + 2 * t;
+                b[ni][0] = *reinterpret_cast<const uint32_t*>(bb);
+                b[ni][1] = *reinterpret_cast<const uint32_t*>(bb + 8);
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh)
+                op.store(m0 + wm + mi * 16 + gq + 8 * hh, n0 + wn + ni * 8 + 2 * t,
+                         acc[mi][ni][2 * hh], acc[mi][ni][2 * hh + 1], (int)blockIdx.z);
+}
+
+template <class Op>
+cudaError_t launch_gemm(const Op& op, long long kchunk, int splits, cudaStream_t s) {
+    const long long gm = (op.M() + BM - 1) / BM;
+    const int gn = (op.N() + BN - 1) / BN;
+    if (gm > 0x7fffffffLL) return cudaErrorInvalidValue;
+    gemm_kernel<Op><<<dim3((unsigned)gm, gn, splits), kGemmThreads, 0, s>>>(op, kchunk);
+    return cudaGetLastError();
+}
+
+// ---- elementwise and reduction kernels ----
+
+__global__ void relu_mask_kernel(const bf16* out, const bf16* g, bf16* gpre, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        gpre[i] = __bfloat162float(out[i]) > 0.0f ? g[i] : __float2bfloat16_rn(0.0f);
+}
+
+// 2x2 average: (((x00 + x10) + x01) + x11) / 4, rounded once.
+__global__ void pool_kernel(const bf16* in, bf16* out, int n, int h, int w, int c) {
+    const int ho = h / 2, wo = w / 2;
+    const long long total = (long long)n * ho * wo * c;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % c);
+        long long r = i / c;
+        const int x = (int)(r % wo);
+        r /= wo;
+        const int y = (int)(r % ho);
+        const int nn = (int)(r / ho);
+        auto at = [&](int yy, int xx) {
+            return __bfloat162float(in[(((long long)nn * h + yy) * w + xx) * c + ch]);
+        };
+        const float s = ((at(2 * y, 2 * x) + at(2 * y + 1, 2 * x)) + at(2 * y, 2 * x + 1)) +
+                        at(2 * y + 1, 2 * x + 1);
+        out[i] = __float2bfloat16_rn(0.25f * s);
+    }
+}
+
+// gin(2y+a, 2x+b) = 0.25 g(y, x) + gin(2y+a, 2x+b) (the skip gradient already there)
+__global__ void pool_back_kernel(const bf16* g, bf16* gin, int n, int h, int w, int c,
+                                 int accumulate) {
+    const long long total = (long long)n * h * w * c;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % c);
+        long long r = i / c;
+        const int x = (int)(r % w);
+        r /= w;
+        const int y = (int)(r % h);
+        const int nn = (int)(r / h);
+        const float v =
+            0.25f * __bfloat162float(g[(((long long)nn * (h / 2) + y / 2) * (w / 2) + x / 2) * c + ch]);
+        gin[i] = __float2bfloat16_rn(accumulate ? v + __bfloat162float(gin[i]) : v);
+    }
+}
+
+__global__ void up_kernel(const bf16* in, bf16* out, int n, int h, int w, int c) {
+    // out is (n, 2h, 2w, c)
+    const long long total = (long long)n * 4 * h * w * c;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % c);
+        long long r = i / c;
+        const int x = (int)(r % (2 * w));
+        r /= 2 * w;
+        const int y = (int)(r % (2 * h));
+        const int nn = (int)(r / (2 * h));
+        out[i] = in[(((long long)nn * h + y / 2) * w + x / 2) * c + ch];
+    }
+}
+
+// gin(y, x) = ((g(2y,2x) + g(2y+1,2x)) + g(2y,2x+1)) + g(2y+1,2x+1), rounded once
+__global__ void up_back_kernel(const bf16* g, bf16* gin, int n, int h, int w, int c) {
+    const long long total = (long long)n * h * w * c;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % c);
+        long long r = i / c;
+        const int x = (int)(r % w);
+        r /= w;
+        const int y = (int)(r % h);
+        const int nn = (int)(r / h);
+        auto at = [&](int yy, int xx) {
+            return __bfloat162float(g[(((long long)nn * 2 * h + yy) * 2 * w + xx) * c + ch]);
+        };
+        gin[i] = __float2bfloat16_rn(((at(2 * y, 2 * x) + at(2 * y + 1, 2 * x)) +
+                                      at(2 * y, 2 * x + 1)) + at(2 * y + 1, 2 * x + 1));
+    }
+}
+
+__global__ void add_kernel(const bf16* a, const bf16* b, bf16* out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(__bfloat162float(a[i]) + __bfloat162float(b[i]));
+}
+
+// host float inputs (n, h, w, 4) -> bf16 (n, h, w, 8) with zero channels 4..7
+__global__ void pack_input_kernel(const float* x, bf16* out, long long pixels, int cin, int cp) {
+    const long long total = pixels * cp;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % cp);
+        const long long p = i / cp;
+        out[i] = __float2bfloat16_rn(ch < cin ? x[p * cin + ch] : 0.0f);
+    }
+}
+
+__global__ void unpack_output_kernel(const bf16* y, float* out, long long pixels, int cout,
+                                     int cp) {
+    const long long total = pixels * cout;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(i % cout);
+        const long long p = i / cout;
+        out[i] = __bfloat162float(y[p * cp + ch]);
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ V block_sum(V v) {
+    __shared__ V sh[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    V s = V(0);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x / 32); ++i) s += sh[i];
+    return s;  // valid in thread 0
+}
+
+// Masked squared error: per-block partial sums (FP64) and the output gradient
+// 2 (y - t) fluid / cnt, stored BF16 in the padded layout.
+__global__ void __launch_bounds__(kThreads) loss_kernel(const bf16* y, const float* t,
+                                                        const uint8_t* fluid, bf16* gy,
+                                                        double* part, long long pixels,
+                                                        int cout, int cp, float inv_cnt) {
+    double s = 0.0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < pixels;
+         p += (long long)gridDim.x * blockDim.x) {
+        const float m = fluid[p] ? 1.0f : 0.0f;
+        for (int c = 0; c < cp; ++c) {
+            float gv = 0.0f;
+            if (c < cout) {
+                const float d = (__bfloat162float(y[p * cp + c]) - t[p * cout + c]) * m;
+                s += (double)d * (double)d;
+                gv = 2.0f * d * inv_cnt;
+            }
+            gy[p * cp + c] = __float2bfloat16_rn(gv);
+        }
+    }
+    const double b = block_sum(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+__global__ void __launch_bounds__(kThreads) sum_kernel(const double* part, int n, double* out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    const double b = block_sum(s);
+    if (threadIdx.x == 0) *out = b;
+}
+
+// bias gradient: gb[co] = sum_p gpre[p][co], one block per channel
+__global__ void __launch_bounds__(kThreads) bias_grad_kernel(const bf16* gpre, float* gb,
+                                                             long long pixels, int cout) {
+    const int co = blockIdx.x;
+    float s = 0.0f;
+    for (long long p = threadIdx.x; p < pixels; p += blockDim.x)
+        s += __bfloat162float(gpre[p * cout + co]);
+    const float b = block_sum(s);
+    if (threadIdx.x == 0) gb[co] = b;
+}
+
+// dW = sum over the splits in order
+__global__ void split_sum_kernel(const float* part, float* gw, int splits, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int z = 0; z < splits; ++z) s += part[(long long)z * n + i];
+        gw[i] = s;
+    }
+}
+
+// Adam on FP32 masters; counts t from 1.
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, long long n,
+                            float lr, float b1, float b2, float c1, float c2, float eps) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// BF16 copies of the weights: wf[co][tap][ci] and wd[ci][tap][co] from the
+// master wm[co][tap][ci]
+__global__ void weight_copies_kernel(const float* wm, bf16* wf, bf16* wd, int cin, int cout) {
+    const long long n = 9LL * cin * cout;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)(i % cin);
+        const long long r = i / cin;
+        const int tap = (int)(r % 9);
+        const int co = (int)(r / 9);
+        const bf16 v = __float2bfloat16_rn(wm[i]);
+        wf[i] = v;
+        wd[((long long)ci * 9 + tap) * cout + co] = v;
+    }
+}
+
+int grid_of(long long n) {
+    long long b = (n + kThreads - 1) / kThreads;
+    return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct lbm_nn {
+    struct Tensor {
+        int h, w, c, cp;   // grid, logical and padded channels
+        bf16* v = nullptr; // activation
+        bf16* g = nullptr; // its gradient
+    };
+    struct Conv {
+        int in, out, relu;
+        int cin, cout, cinp, coutp;
+        float *wm, *bm, *gw, *gb, *mw, *vw, *mb, *vb;  // [coutp][9][cinp], [coutp]
+        bf16 *wf, *wd;
+    };
+    enum Kind { CONV, POOL, UP, ADD };
+    struct Op {
+        Kind k;
+        int a, b, out;  // tensor ids (CONV: conv index in a)
+    };
+    int L = 0, nb = 0, H = 0, W = 0;
+    std::vector<int> ch;
+    std::vector<Tensor> t;
+    std::vector<Conv> conv;
+    std::vector<Op> ops;
+    int x_id = 0, y_id = 0;
+    cudaStream_t stream = nullptr;
+    float* pbuf = nullptr;     // all FP32 parameter-sized arrays
+    size_t pfloats = 0;
+    bf16* wbuf = nullptr;      // BF16 weight copies
+    unsigned char* abuf = nullptr;  // activations and gradients
+    bf16* scratch = nullptr;   // relu-masked gradient
+    float* part = nullptr;     // weight-gradient split partials
+    size_t part_floats = 0;
+    double* dpart = nullptr;   // loss partials (+1 for the total)
+    float* xin = nullptr;      // staging of host inputs (float)
+    float* tgt = nullptr;
+    uint8_t* fl = nullptr;
+    float* yout = nullptr;
+    long long adam_t = 0;
+    int64_t launches = 0;
+    char err[512] = {0};
+};
+
+namespace {
+
+thread_local char g_nn_err[512] = "no error";
+
+void nn_err(lbm_nn* nn, const char* fmt, ...) {
+    char* dst = nn ? nn->err : g_nn_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+}
+
+#define NCK(nn, call, what)                                                    \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            nn_err(nn, "%s: %s", what, cudaGetErrorString(e_));                \
+            return e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA; \
+        }                                                                      \
+    } while (0)
+
+int pad8(int c) { return (c + 7) / 8 * 8; }
+
+long long pixels(const lbm_nn* nn, int id, int n) {
+    return (long long)n * nn->t[id].h * nn->t[id].w;
+}
+
+int add_tensor(lbm_nn* nn, int h, int w, int c) {
+    lbm_nn::Tensor T;
+    T.h = h;
+    T.w = w;
+    T.c = c;
+    T.cp = pad8(c);
+    nn->t.push_back(T);
+    return (int)nn->t.size() - 1;
+}
+
+int add_conv(lbm_nn* nn, int in, int cout, int relu) {
+    const lbm_nn::Tensor X = nn->t[in];  // a copy: add_tensor grows nn->t
+    const int out = add_tensor(nn, X.h, X.w, cout);
+    lbm_nn::Conv c{};
+    c.in = in;
+    c.out = out;
+    c.relu = relu;
+    c.cin = X.c;
+    c.cout = cout;
+    c.cinp = X.cp;
+    c.coutp = pad8(cout);
+    nn->conv.push_back(c);
+    nn->ops.push_back({lbm_nn::CONV, (int)nn->conv.size() - 1, 0, out});
+    return out;
+}
+
+// Builds the network graph (see include/lbm_nn.h).
+void build_graph(lbm_nn* nn) {
+    nn->x_id = add_tensor(nn, nn->H, nn->W, 4);
+    int x = nn->x_id;
+    std::vector<int> e(nn->L);
+    int h = nn->H, w = nn->W;
+    for (int l = 0; l < nn->L; ++l) {
+        x = add_conv(nn, x, nn->ch[l], 1);
+        x = add_conv(nn, x, nn->ch[l], 1);
+        e[l] = x;
+        if (l < nn->L - 1) {
+            h /= 2;
+            w /= 2;
+            const int p = add_tensor(nn, h, w, nn->ch[l]);
+            nn->ops.push_back({lbm_nn::POOL, x, 0, p});
+            x = p;
+        }
+    }
+    for (int l = nn->L - 2; l >= 0; --l) {
+        h *= 2;
+        w *= 2;
+        const int u = add_tensor(nn, h, w, nn->ch[l + 1]);
+        nn->ops.push_back({lbm_nn::UP, x, 0, u});
+        const int c = add_conv(nn, u, nn->ch[l], 1);
+        const int s = add_tensor(nn, h, w, nn->ch[l]);
+        nn->ops.push_back({lbm_nn::ADD, c, e[l], s});
+        x = add_conv(nn, s, nn->ch[l], 1);
+    }
+    nn->y_id = add_conv(nn, x, 3, 0);
+}
+
+size_t conv_wsize(const lbm_nn::Conv& c) { return 9ull * c.cinp * c.coutp; }
+
+lbm_status sync_weights(lbm_nn* nn) {
+    for (auto& c : nn->conv) {
+        weight_copies_kernel<<<grid_of((long long)conv_wsize(c)), kThreads, 0, nn->stream>>>(
+            c.wm, c.wf, c.wd, c.cinp, c.coutp);
+        NCK(nn, cudaGetLastError(), "weight copies");
+        ++nn->launches;
+    }
+    return LBM_OK;
+}
+
+lbm_status upload_inputs(lbm_nn* nn, const float* x, const float* tgt, const uint8_t* fluid,
+                         int n) {
+    const long long P = (long long)n * nn->H * nn->W;
+    NCK(nn, cudaMemcpyAsync(nn->xin, x, P * 4 * sizeof(float), cudaMemcpyHostToDevice, nn->stream),
+        "cudaMemcpyAsync(H2D)");
+    if (tgt)
+        NCK(nn, cudaMemcpyAsync(nn->tgt, tgt, P * 3 * sizeof(float), cudaMemcpyHostToDevice,
+                                nn->stream),
+            "cudaMemcpyAsync(H2D)");
+    if (fluid)
+        NCK(nn, cudaMemcpyAsync(nn->fl, fluid, P, cudaMemcpyHostToDevice, nn->stream),
+            "cudaMemcpyAsync(H2D)");
+    const lbm_nn::Tensor& X = nn->t[nn->x_id];
+    pack_input_kernel<<<grid_of(P * X.cp), kThreads, 0, nn->stream>>>(nn->xin, X.v, P, 4, X.cp);
+    NCK(nn, cudaGetLastError(), "input packing");
+    ++nn->launches;
+    return LBM_OK;
+}
+
+lbm_status forward(lbm_nn* nn, int n) {
+    const cudaStream_t s = nn->stream;
+    for (const auto& op : nn->ops) {
+        cudaError_t e = cudaSuccess;
+        if (op.k == lbm_nn::CONV) {
+            const lbm_nn::Conv& c = nn->conv[op.a];
+            const lbm_nn::Tensor& X = nn->t[c.in];
+            FwdOp f;
+            f.g = Geo{n, X.h, X.w, pixels(nn, c.in, n)};
+            f.in = X.v;
+            f.wf = c.wf;
+            f.bias = c.bm;
+            f.out = nn->t[c.out].v;
+            f.cin = c.cinp;
+            f.cout = c.coutp;
+            f.relu = c.relu;
+            e = launch_gemm(f, f.K(), 1, s);
+        } else if (op.k == lbm_nn::POOL) {
+            const lbm_nn::Tensor& X = nn->t[op.a];
+            pool_kernel<<<grid_of(pixels(nn, op.out, n) * X.cp), kThreads, 0, s>>>(
+                X.v, nn->t[op.out].v, n, X.h, X.w, X.cp);
+            e = cudaGetLastError();
+        } else if (op.k == lbm_nn::UP) {
+            const lbm_nn::Tensor& X = nn->t[op.a];
+            up_kernel<<<grid_of(pixels(nn, op.out, n) * X.cp), kThreads, 0, s>>>(
+                X.v, nn->t[op.out].v, n, X.h, X.w, X.cp);
+            e = cudaGetLastError();
+        } else {
+            const long long cnt = pixels(nn, op.out, n) * nn->t[op.out].cp;
+            add_kernel<<<grid_of(cnt), kThreads, 0, s>>>(nn->t[op.a].v, nn->t[op.b].v,
+                                                         nn->t[op.out].v, cnt);
+            e = cudaGetLastError();
+        }
+        NCK(nn, e, "forward kernels");
+        ++nn->launches;
+    }
+    return LBM_OK;
+}
+
+// Loss of the batch (synchronous) and, through the backward pass, the
+// gradients of every convolution's parameters (c.gw, c.gb).
+lbm_status backward(lbm_nn* nn, int n, float* loss) {
+    const cudaStream_t s = nn->stream;
+    const long long P = (long long)n * nn->H * nn->W;
+    std::vector<uint8_t> host_fl(P);
+    NCK(nn, cudaMemcpyAsync(host_fl.data(), nn->fl, P, cudaMemcpyDeviceToHost, s),
+        "cudaMemcpyAsync(D2H)");
+    NCK(nn, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    long long nf = 0;
+    for (long long i = 0; i < P; ++i) nf += host_fl[i] != 0;
+    const float inv_cnt = nf > 0 ? (float)(1.0 / (3.0 * (double)nf)) : 0.0f;
+    std::vector<bf16*> G(nn->t.size());
+    for (size_t i = 0; i < nn->t.size(); ++i) G[i] = nn->t[i].g;
+    const lbm_nn::Tensor& Y = nn->t[nn->y_id];
+    const int lb = grid_of(P) < 1024 ? grid_of(P) : 1024;
+    loss_kernel<<<lb, kThreads, 0, s>>>(Y.v, nn->tgt, nn->fl, G[nn->y_id], nn->dpart, P, 3, Y.cp,
+                                        inv_cnt);
+    NCK(nn, cudaGetLastError(), "loss kernel");
+    sum_kernel<<<1, kThreads, 0, s>>>(nn->dpart, lb, nn->dpart + 1024);
+    NCK(nn, cudaGetLastError(), "loss sum");
+    nn->launches += 2;
+    std::vector<char> pool_seen(nn->t.size(), 0);
+    for (int i = (int)nn->ops.size() - 1; i >= 0; --i) {
+        const lbm_nn::Op& op = nn->ops[i];
+        cudaError_t e = cudaSuccess;
+        if (op.k == lbm_nn::CONV) {
+            const lbm_nn::Conv& c = nn->conv[op.a];
+            const lbm_nn::Tensor& X = nn->t[c.in];
+            const lbm_nn::Tensor& O = nn->t[c.out];
+            const long long Pc = pixels(nn, c.in, n);
+            const bf16* gpre = G[c.out];
+            if (c.relu) {
+                relu_mask_kernel<<<grid_of(Pc * O.cp), kThreads, 0, s>>>(O.v, G[c.out], nn->scratch,
+                                                                         Pc * O.cp);
+                if ((e = cudaGetLastError()) != cudaSuccess) break;
+                ++nn->launches;
+                gpre = nn->scratch;
+            }
+            // weight gradient, split over pixels
+            const int splits = (int)((Pc + kSplitPixels - 1) / kSplitPixels);
+            WgradOp wg;
+            wg.g = Geo{n, X.h, X.w, Pc};
+            wg.gpre = gpre;
+            wg.in = X.v;
+            wg.part = nn->part;
+            wg.cin = c.cinp;
+            wg.cout = c.coutp;
+            if ((e = launch_gemm(wg, kSplitPixels, splits, s)) != cudaSuccess) break;
+            const long long nw = (long long)conv_wsize(c);
+            split_sum_kernel<<<grid_of(nw), kThreads, 0, s>>>(nn->part, c.gw, splits, nw);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            bias_grad_kernel<<<c.coutp, kThreads, 0, s>>>(gpre, c.gb, Pc, c.coutp);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            nn->launches += 3;
+            if (c.in != nn->x_id) {
+                DgradOp dg;
+                dg.g = wg.g;
+                dg.gpre = gpre;
+                dg.wd = c.wd;
+                dg.gin = G[c.in];
+                dg.cin = c.cinp;
+                dg.cout = c.coutp;
+                if ((e = launch_gemm(dg, dg.K(), 1, s)) != cudaSuccess) break;
+                ++nn->launches;
+            }
+        } else if (op.k == lbm_nn::POOL) {
+            const lbm_nn::Tensor& X = nn->t[op.a];
+            // the skip addition of the decoder has set the gradient of op.a
+            pool_back_kernel<<<grid_of(pixels(nn, op.a, n) * X.cp), kThreads, 0, s>>>(
+                G[op.out], G[op.a], n, X.h, X.w, X.cp, 1);
+            e = cudaGetLastError();
+            ++nn->launches;
+        } else if (op.k == lbm_nn::UP) {
+            const lbm_nn::Tensor& X = nn->t[op.a];
+            up_back_kernel<<<grid_of(pixels(nn, op.a, n) * X.cp), kThreads, 0, s>>>(
+                G[op.out], G[op.a], n, X.h, X.w, X.cp);
+            e = cudaGetLastError();
+            ++nn->launches;
+        } else {
+            // an addition passes its gradient to both inputs
+            G[op.a] = G[op.out];
+            G[op.b] = G[op.out];
+        }
+        if (e != cudaSuccess) {
+            nn_err(nn, "backward kernels: %s", cudaGetErrorString(e));
+            return LBM_ERR_CUDA;
+        }
+    }
+    double l = 0.0;
+    NCK(nn, cudaMemcpyAsync(&l, nn->dpart + 1024, sizeof(double), cudaMemcpyDeviceToHost, s),
+        "cudaMemcpyAsync(D2H)");
+    NCK(nn, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (loss) *loss = (float)(l * (double)inv_cnt);
+    return LBM_OK;
+}
+
+bool bad_batch(lbm_nn* nn, int n) {
+    if (n < 1 || n > nn->nb) {
+        nn_err(nn, "batch size %d outside [1, %d]", n, nn->nb);
+        return true;
+    }
+    return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_nn_create(int levels, const int* channels, int max_batch, int height, int width,
+                         uint64_t seed, void* cuda_stream, lbm_nn** out) {
+    if (!out) {
+        nn_err(nullptr, "out is NULL");
+        return LBM_ERR_INVALID;
+    }
+    *out = nullptr;
+    if (levels < 1 || levels > 6 || !channels || max_batch < 1 || height < 1 || width < 1 ||
+        height > 4096 || width > 4096 || height % (1 << (levels - 1)) ||
+        width % (1 << (levels - 1))) {
+        nn_err(nullptr, "invalid network shape (levels 1..6, height and width multiples of "
+                        "2^(levels-1), at most 4096)");
+        return LBM_ERR_INVALID;
+    }
+    for (int l = 0; l < levels; ++l)
+        if (channels[l] < 1 || channels[l] > 512) {
+            nn_err(nullptr, "channels must lie in [1, 512]");
+            return LBM_ERR_INVALID;
+        }
+    if ((double)max_batch * height * width > 1.0e8) {
+        nn_err(nullptr, "batch of more than 1e8 cells");
+        return LBM_ERR_INVALID;
+    }
+    lbm_nn* nn = new (std::nothrow) lbm_nn();
+    if (!nn) {
+        nn_err(nullptr, "host allocation failed");
+        return LBM_ERR_OOM;
+    }
+    nn->L = levels;
+    nn->ch.assign(channels, channels + levels);
+    nn->nb = max_batch;
+    nn->H = height;
+    nn->W = width;
+    nn->stream = (cudaStream_t)cuda_stream;
+    build_graph(nn);
+    auto fail = [&](lbm_status s) {
+        std::snprintf(g_nn_err, sizeof(g_nn_err), "%s", nn->err);
+        lbm_nn_destroy(nn);
+        return s;
+    };
+#define NCKC(call, what)                                                        \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) {                                                \
+            nn_err(nn, "%s: %s", what, cudaGetErrorString(e_));                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA); \
+        }                                                                       \
+    } while (0)
+    // parameters: 8 FP32 arrays per convolution (w, b, gw, gb, mw, vw, mb, vb)
+    size_t pf = 0, wb = 0, maxw = 0;
+    for (auto& c : nn->conv) {
+        pf += 4 * (conv_wsize(c) + c.coutp);
+        wb += 2 * conv_wsize(c);
+        maxw = conv_wsize(c) > maxw ? conv_wsize(c) : maxw;
+    }
+    nn->pfloats = pf;
+    NCKC(cudaMalloc(&nn->pbuf, pf * sizeof(float)), "cudaMalloc(parameters)");
+    NCKC(cudaMemsetAsync(nn->pbuf, 0, pf * sizeof(float), nn->stream), "cudaMemset");
+    NCKC(cudaMalloc(&nn->wbuf, wb * sizeof(bf16)), "cudaMalloc(weights)");
+    {
+        float* q = nn->pbuf;
+        bf16* r = nn->wbuf;
+        for (auto& c : nn->conv) {
+            const size_t w = conv_wsize(c), b = c.coutp;
+            c.wm = q; q += w;
+            c.gw = q; q += w;
+            c.mw = q; q += w;
+            c.vw = q; q += w;
+            c.bm = q; q += b;
+            c.gb = q; q += b;
+            c.mb = q; q += b;
+            c.vb = q; q += b;
+            c.wf = r; r += w;
+            c.wd = r; r += w;
+        }
+    }
+    // activations and their gradients, 256-byte aligned parts
+    size_t ab = 0, maxt = 0;
+    for (auto& T : nn->t) {
+        const size_t e = (size_t)nn->nb * T.h * T.w * T.cp;
+        ab += 2 * ((e * sizeof(bf16) + 255) / 256 * 256);
+        maxt = e > maxt ? e : maxt;
+    }
+    NCKC(cudaMalloc(&nn->abuf, ab), "cudaMalloc(activations)");
+    NCKC(cudaMemsetAsync(nn->abuf, 0, ab, nn->stream), "cudaMemset");
+    {
+        unsigned char* q = nn->abuf;
+        for (auto& T : nn->t) {
+            const size_t e = ((size_t)nn->nb * T.h * T.w * T.cp * sizeof(bf16) + 255) / 256 * 256;
+            T.v = reinterpret_cast<bf16*>(q);
+            q += e;
+            T.g = reinterpret_cast<bf16*>(q);
+            q += e;
+        }
+    }
+    NCKC(cudaMalloc(&nn->scratch, maxt * sizeof(bf16)), "cudaMalloc(scratch)");
+    const long long Pmax = (long long)nn->nb * nn->H * nn->W;
+    const long long splits = (Pmax + kSplitPixels - 1) / kSplitPixels;
+    nn->part_floats = (size_t)splits * maxw;
+    NCKC(cudaMalloc(&nn->part, nn->part_floats * sizeof(float)), "cudaMalloc(partials)");
+    NCKC(cudaMalloc(&nn->dpart, 1025 * sizeof(double)), "cudaMalloc(loss)");
+    NCKC(cudaMalloc(&nn->xin, Pmax * 4 * sizeof(float)), "cudaMalloc(inputs)");
+    NCKC(cudaMalloc(&nn->tgt, Pmax * 3 * sizeof(float)), "cudaMalloc(targets)");
+    NCKC(cudaMalloc(&nn->fl, Pmax), "cudaMalloc(fluid)");
+    NCKC(cudaMalloc(&nn->yout, Pmax * 3 * sizeof(float)), "cudaMalloc(outputs)");
+#undef NCKC
+    // He-normal initial weights (host generator), zero biases
+    std::vector<float> params(lbm_nn_param_count(nn));
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<double> N01(0.0, 1.0);
+    size_t k = 0;
+    for (auto& c : nn->conv) {
+        const double sd = std::sqrt(2.0 / (9.0 * c.cin));
+        for (size_t i = 0; i < 9ull * c.cin * c.cout; ++i) params[k++] = (float)(sd * N01(rng));
+        for (int i = 0; i < c.cout; ++i) params[k++] = 0.0f;
+    }
+    lbm_status st = lbm_nn_set_params(nn, params.data());
+    if (st != LBM_OK) return fail(st);
+    *out = nn;
+    return LBM_OK;
+}
+
+void lbm_nn_destroy(lbm_nn* nn) {
+    if (!nn) return;
+    cudaFree(nn->pbuf);
+    cudaFree(nn->wbuf);
+    cudaFree(nn->abuf);
+    cudaFree(nn->scratch);
+    cudaFree(nn->part);
+    cudaFree(nn->dpart);
+    cudaFree(nn->xin);
+    cudaFree(nn->tgt);
+    cudaFree(nn->fl);
+    cudaFree(nn->yout);
+    delete nn;
+}
+
+size_t lbm_nn_param_count(const lbm_nn* nn) {
+    if (!nn) return 0;
+    size_t n = 0;
+    for (auto& c : nn->conv) n += 9ull * c.cin * c.cout + c.cout;
+    return n;
+}
+
+// Host parameter vector (dy, dx, cin, cout per convolution, then biases) <->
+// device masters [coutp][tap][cinp].
+static lbm_status transfer_params(lbm_nn* nn, float* host, bool to_device, bool grads) {
+    for (auto& c : nn->conv) {
+        const size_t w = conv_wsize(c);
+        std::vector<float> dev(w + c.coutp, 0.0f);
+        float* dw = grads ? c.gw : c.wm;
+        float* db = grads ? c.gb : c.bm;
+        if (!to_device) {
+            NCK(nn, cudaMemcpyAsync(dev.data(), dw, w * sizeof(float), cudaMemcpyDeviceToHost,
+                                    nn->stream),
+                "cudaMemcpyAsync(D2H)");
+            NCK(nn, cudaMemcpyAsync(dev.data() + w, db, c.coutp * sizeof(float),
+                                    cudaMemcpyDeviceToHost, nn->stream),
+                "cudaMemcpyAsync(D2H)");
+            NCK(nn, cudaStreamSynchronize(nn->stream), "cudaStreamSynchronize");
+        }
+        for (int tap = 0; tap < 9; ++tap)
+            for (int ci = 0; ci < c.cin; ++ci)
+                for (int co = 0; co < c.cout; ++co) {
+                    float& h = host[((size_t)tap * c.cin + ci) * c.cout + co];
+                    float& d = dev[((size_t)co * 9 + tap) * c.cinp + ci];
+                    if (to_device) d = h;
+                    else h = d;
+                }
+        host += 9ull * c.cin * c.cout;
+        for (int co = 0; co < c.cout; ++co) {
+            if (to_device) dev[w + co] = host[co];
+            else host[co] = dev[w + co];
+        }
+        host += c.cout;
+        if (to_device) {
+            NCK(nn, cudaMemcpyAsync(dw, dev.data(), w * sizeof(float), cudaMemcpyHostToDevice,
+                                    nn->stream),
+                "cudaMemcpyAsync(H2D)");
+            NCK(nn, cudaMemcpyAsync(db, dev.data() + w, c.coutp * sizeof(float),
+                                    cudaMemcpyHostToDevice, nn->stream),
+                "cudaMemcpyAsync(H2D)");
+            NCK(nn, cudaStreamSynchronize(nn->stream), "cudaStreamSynchronize");
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_nn_get_params(lbm_nn* nn, float* params) {
+    if (!nn || !params) return LBM_ERR_INVALID;
+    return transfer_params(nn, params, false, false);
+}
+
+lbm_status lbm_nn_set_params(lbm_nn* nn, const float* params) {
+    if (!nn || !params) return LBM_ERR_INVALID;
+    lbm_status s = transfer_params(nn, const_cast<float*>(params), true, false);
+    if (s != LBM_OK) return s;
+    for (auto& c : nn->conv) {
+        const size_t w = conv_wsize(c);
+        NCK(nn, cudaMemsetAsync(c.mw, 0, w * sizeof(float), nn->stream), "cudaMemset");
+        NCK(nn, cudaMemsetAsync(c.vw, 0, w * sizeof(float), nn->stream), "cudaMemset");
+        NCK(nn, cudaMemsetAsync(c.mb, 0, c.coutp * sizeof(float), nn->stream), "cudaMemset");
+        NCK(nn, cudaMemsetAsync(c.vb, 0, c.coutp * sizeof(float), nn->stream), "cudaMemset");
+    }
+    nn->adam_t = 0;
+    s = sync_weights(nn);
+    if (s != LBM_OK) return s;
+    NCK(nn, cudaStreamSynchronize(nn->stream), "cudaStreamSynchronize");
+    return LBM_OK;
+}
+
+lbm_status lbm_nn_forward(lbm_nn* nn, const float* x, int n, float* y) {
+    if (!nn || !x || !y) return LBM_ERR_INVALID;
+    if (bad_batch(nn, n)) return LBM_ERR_INVALID;
+    lbm_status s = upload_inputs(nn, x, nullptr, nullptr, n);
+    if (s == LBM_OK) s = forward(nn, n);
+    if (s != LBM_OK) return s;
+    const long long P = (long long)n * nn->H * nn->W;
+    const lbm_nn::Tensor& Y = nn->t[nn->y_id];
+    unpack_output_kernel<<<grid_of(P * 3), kThreads, 0, nn->stream>>>(Y.v, nn->yout, P, 3, Y.cp);
+    NCK(nn, cudaGetLastError(), "output unpacking");
+    ++nn->launches;
+    NCK(nn, cudaMemcpyAsync(y, nn->yout, P * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                            nn->stream),
+        "cudaMemcpyAsync(D2H)");
+    NCK(nn, cudaStreamSynchronize(nn->stream), "cudaStreamSynchronize");
+    return LBM_OK;
+}
+
+lbm_status lbm_nn_gradients(lbm_nn* nn, const float* x, const float* target,
+                            const uint8_t* fluid, int n, float* loss, float* grads) {
+    if (!nn || !x || !target || !fluid) return LBM_ERR_INVALID;
+    if (bad_batch(nn, n)) return LBM_ERR_INVALID;
+    lbm_status s = upload_inputs(nn, x, target, fluid, n);
+    if (s == LBM_OK) s = forward(nn, n);
+    if (s == LBM_OK) s = backward(nn, n, loss);
+    if (s == LBM_OK && grads) s = transfer_params(nn, grads, false, true);
+    return s;
+}
+
+lbm_status lbm_nn_train_step(lbm_nn* nn, const float* x, const float* target,
+                             const uint8_t* fluid, int n, float lr, float* loss) {
+    if (!nn || !x || !target || !fluid) return LBM_ERR_INVALID;
+    if (bad_batch(nn, n)) return LBM_ERR_INVALID;
+    if (!(lr > 0.0f) || !std::isfinite(lr)) {
+        nn_err(nn, "learning rate must be finite and > 0");
+        return LBM_ERR_INVALID;
+    }
+    lbm_status s = upload_inputs(nn, x, target, fluid, n);
+    if (s == LBM_OK) s = forward(nn, n);
+    if (s == LBM_OK) s = backward(nn, n, loss);
+    if (s != LBM_OK) return s;
+    ++nn->adam_t;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - (float)std::pow(0.9, (double)nn->adam_t);
+    const float c2 = 1.0f - (float)std::pow(0.999, (double)nn->adam_t);
+    for (auto& c : nn->conv) {
+        const long long w = (long long)conv_wsize(c);
+        adam_kernel<<<grid_of(w), kThreads, 0, nn->stream>>>(c.wm, c.gw, c.mw, c.vw, w, lr, b1, b2,
+                                                             c1, c2, 1e-8f);
+        NCK(nn, cudaGetLastError(), "adam");
+        adam_kernel<<<grid_of(c.coutp), kThreads, 0, nn->stream>>>(c.bm, c.gb, c.mb, c.vb, c.coutp,
+                                                                   lr, b1, b2, c1, c2, 1e-8f);
+        NCK(nn, cudaGetLastError(), "adam");
+        nn->launches += 2;
+    }
+    s = sync_weights(nn);
+    if (s != LBM_OK) return s;
+    NCK(nn, cudaStreamSynchronize(nn->stream), "cudaStreamSynchronize");
+    return LBM_OK;
+}
+
+int64_t lbm_nn_launch_count(const lbm_nn* nn) { return nn ? nn->launches : -1; }
+
+const char* lbm_nn_last_error(const lbm_nn* nn) { return nn ? nn->err : g_nn_err; }
+
+}  // extern "C"

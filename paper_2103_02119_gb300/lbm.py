@@ -115,6 +115,25 @@ def _load():
     L.lbm_batch_launch_count.restype = I64
     L.lbm_batch_last_error.argtypes = [_P]
     L.lbm_batch_last_error.restype = ctypes.c_char_p
+    _F = ctypes.POINTER(ctypes.c_float)
+    L.lbm_nn_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P,
+                                ctypes.POINTER(_P)]
+    L.lbm_nn_destroy.argtypes = [_P]
+    L.lbm_nn_destroy.restype = None
+    L.lbm_nn_param_count.argtypes = [_P]
+    L.lbm_nn_param_count.restype = ctypes.c_size_t
+    L.lbm_nn_get_params.argtypes = [_P, _F]
+    L.lbm_nn_set_params.argtypes = [_P, _F]
+    L.lbm_nn_forward.argtypes = [_P, _F, ctypes.c_int, _F]
+    L.lbm_nn_gradients.argtypes = [_P, _F, _F, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int,
+                                   _F, _F]
+    L.lbm_nn_train_step.argtypes = [_P, _F, _F, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int,
+                                    ctypes.c_float, _F]
+    L.lbm_nn_launch_count.argtypes = [_P]
+    L.lbm_nn_launch_count.restype = ctypes.c_int64
+    L.lbm_nn_last_error.argtypes = [_P]
+    L.lbm_nn_last_error.restype = ctypes.c_char_p
     return L
 
 
@@ -460,6 +479,100 @@ def lbm_batch_launch_count(b) -> int:
 
 def lbm_batch_last_error(b=None) -> str:
     return lib.lbm_batch_last_error(b).decode()
+
+
+# ---------------------------------------------------------- surrogate ABI --
+
+def _ncheck(status: int, nn=None):
+    if status != LBM_OK:
+        raise LbmError(status, lib.lbm_nn_last_error(nn).decode())
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def lbm_nn_create(channels, max_batch, height, width, seed=0, stream=None):
+    ch = (ctypes.c_int * len(channels))(*[int(c) for c in channels])
+    nn = _P()
+    _ncheck(lib.lbm_nn_create(len(channels), ch, int(max_batch), int(height), int(width),
+                              int(seed), _stream_ptr(stream), ctypes.byref(nn)), None)
+    return nn
+
+
+def lbm_nn_destroy(nn):
+    lib.lbm_nn_destroy(nn)
+
+
+def lbm_nn_param_count(nn) -> int:
+    return int(lib.lbm_nn_param_count(nn))
+
+
+def lbm_nn_get_params(nn):
+    out = np.empty(lbm_nn_param_count(nn), np.float32)
+    _ncheck(lib.lbm_nn_get_params(nn, _fptr(out)), nn)
+    return out
+
+
+def lbm_nn_set_params(nn, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != lbm_nn_param_count(nn):
+        raise ValueError("parameter vector of the wrong length")
+    _ncheck(lib.lbm_nn_set_params(nn, _fptr(p)), nn)
+
+
+def lbm_nn_forward(nn, x):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty(x.shape[:3] + (3,), np.float32)
+    _ncheck(lib.lbm_nn_forward(nn, _fptr(x), x.shape[0], _fptr(y)), nn)
+    return y
+
+
+def lbm_nn_gradients(nn, x, target, fluid):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    t = np.ascontiguousarray(target, dtype=np.float32)
+    f = np.ascontiguousarray(fluid, dtype=np.uint8)
+    loss = ctypes.c_float()
+    g = np.empty(lbm_nn_param_count(nn), np.float32)
+    _ncheck(lib.lbm_nn_gradients(nn, _fptr(x), _fptr(t),
+                                 f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), x.shape[0],
+                                 ctypes.byref(loss), _fptr(g)), nn)
+    return float(loss.value), g
+
+
+def lbm_nn_train_step(nn, x, target, fluid, lr):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    t = np.ascontiguousarray(target, dtype=np.float32)
+    f = np.ascontiguousarray(fluid, dtype=np.uint8)
+    loss = ctypes.c_float()
+    _ncheck(lib.lbm_nn_train_step(nn, _fptr(x), _fptr(t),
+                                  f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), x.shape[0],
+                                  float(lr), ctypes.byref(loss)), nn)
+    return float(loss.value)
+
+
+def lbm_nn_launch_count(nn) -> int:
+    return int(lib.lbm_nn_launch_count(nn))
+
+
+def lbm_nn_last_error(nn=None) -> str:
+    return lib.lbm_nn_last_error(nn).decode()
+
+
+def params_to_list(vec, shapes):
+    """Flat parameter vector -> [(w (3, 3, cin, cout), b (cout,))]."""
+    out, k = [], 0
+    for ci, co in shapes:
+        w = np.asarray(vec[k:k + 9 * ci * co], dtype=np.float64).reshape(3, 3, ci, co)
+        k += 9 * ci * co
+        b = np.asarray(vec[k:k + co], dtype=np.float64)
+        k += co
+        out.append((w, b))
+    return out
+
+
+def params_to_vec(params):
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in params])
 
 
 # ------------------------------------------------------------ convenience --

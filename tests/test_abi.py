@@ -11,6 +11,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "lbm.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("lbm.h", "lbm_nn.h")]
 
 
 @pytest.fixture(scope="module")
@@ -22,7 +23,7 @@ def L():
 
 
 def declared():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
 
@@ -145,3 +146,14 @@ def test_batch_null_arguments(L):
     assert L.lib.lbm_batch_is_active(None, 0) == -1
     assert L.lib.lbm_batch_step_count(None, 0) == -1
     L.lib.lbm_batch_destroy(None)  # ignored
+
+
+def test_nn_invalid_shapes_rejected_on_host(L):
+    for args in [([8, 16], 0, 16, 16), ([8, 16], 2, 15, 16), ([8, 0], 2, 16, 16),
+                 ([8] * 7, 2, 128, 128), ([600], 2, 16, 16)]:
+        with pytest.raises(L.LbmError) as e:
+            L.lbm_nn_create(*args)
+        assert e.value.status == L.LBM_ERR_INVALID
+    assert L.lib.lbm_nn_param_count(None) == 0
+    assert L.lib.lbm_nn_forward(None, None, 1, None) == L.LBM_ERR_INVALID
+    L.lib.lbm_nn_destroy(None)
