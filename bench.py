@@ -53,10 +53,16 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-sweep measurements")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched-sweep throughput (for profiling)")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--ttr-count", type=int, default=64)
     ap.add_argument("--ttr-max-steps", type=int, default=60000)
+    ap.add_argument("--no-warm", action="store_true",
+                    help="skip the learned warm-start measurement")
+    ap.add_argument("--warm-train", type=int, default=1024)
+    ap.add_argument("--warm-epochs", type=int, default=60)
     ap.add_argument("--block-x", type=int, default=0)
     ap.add_argument("--bands", type=int, default=0)
     return ap.parse_args()
@@ -157,7 +163,7 @@ def measured_peaks():
 
 def step_kernel_hash():
     h = hashlib.sha256()
-    for f in ("rc_step.cu", "lbm_device.cuh"):
+    for f in ("rc_step.cu", "rnr_step.cu", "step_block.cuh", "lbm_device.cuh"):
         with open(os.path.join(ROOT, "paper_2103_02119_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -330,6 +336,48 @@ def batch_time_to_residual(torch, count, max_steps, tol=1e-8, check=100):
             "sequential_max_steps": max(steps_s), "speedup": ts / tb}
 
 
+# ---------------------------------------------------------------- warm start --
+
+def warm_start_measure(torch, ntrain, epochs, n=32, ntest=32):
+    """Trains the surrogate on steady cavities from the batched solver, then
+    runs held-out instances to R <= 1e-8 from the rest state and from the
+    network's prediction (both as one batch each)."""
+    import numpy as np
+    from paper_2103_02119_gb300 import warmstart as WS
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    wls, x, t, fl, _ = WS.build_dataset(ntrain, seed=0, n=n, stream=stream)
+    t_data = time.perf_counter() - t0
+    ws = WS.WarmStart([32, 64, 128, 256], n=n, max_batch=32, seed=0, stream=stream)
+    t0 = time.perf_counter()
+    hist = ws.train(x, t, fl, epochs=epochs, lr=2e-3, lr_final=2e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    test = WS.cavity_set(ntest, seed=1, n=n)
+    tx = WS.inputs_of(test)
+    t0 = time.perf_counter()
+    y = ws.predict(tx)
+    t_pred = time.perf_counter() - t0
+    rest = WS.solve(test, stream=stream)
+    warm = WS.solve(test, inits=[WS.fields_of(w, y[k]) for k, w in enumerate(test)],
+                    stream=stream)
+    tt = np.stack([WS.targets_of(w, *rest["fields"][k]) for k, w in enumerate(test)])
+    m = WS.fluid_of(test)[..., None].astype(bool)
+    rms = float(np.sqrt(((y - tt) ** 2 * m).sum() / (3 * m.sum())))
+    ws.close()
+    return {"instances": f"{n}x{n} lid-driven cavities with obstacles, a in [0.5, 1], "
+                         "Re in [20, 200], seeded; train seed 0, test seed 1",
+            "network": "4-level conv encoder-decoder, 32-256 channels, BF16 mma.sync",
+            "train_instances": len(wls), "epochs": epochs, "final_train_loss": hist[-1],
+            "test_instances": ntest, "test_rms_error": rms,
+            "data_seconds": t_data, "train_seconds": t_train,
+            "predict_seconds": t_pred, "tol": 1e-8,
+            "rest_steps_mean": float(rest["steps"].mean()),
+            "warm_steps_mean": float(warm["steps"].mean()),
+            "rest_seconds": rest["seconds"], "warm_seconds": warm["seconds"] + t_pred,
+            "steps_ratio_warm_over_rest": float(warm["steps"].mean() / rest["steps"].mean())}
+
+
 # -------------------------------------------------------------- oracle arm --
 
 def oracle_mlups(wl, rows, seconds, warmup_steps=0, steps=None):
@@ -399,6 +447,12 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    if args.batch_only:
+        if rank == 0:
+            print(json.dumps(batch_throughput(torch, args.batch_count, args.batch_steps)),
+                  flush=True)
+        return
+
     from paper_2103_02119_gb300.lbm import Lattice
     wl = workload(args)
     stream = torch.cuda.current_stream()
@@ -439,6 +493,10 @@ def main():
         batch["time_to_residual"] = batch_time_to_residual(torch, args.ttr_count,
                                                            args.ttr_max_steps)
 
+    warm = None
+    if rank == 0 and not args.no_warm:
+        warm = warm_start_measure(torch, args.warm_train, args.warm_epochs)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         mlups, threads, steps, desc, _ = oracle_mlups(wl, wl.ny, args.cpu_seconds)
@@ -453,7 +511,7 @@ def main():
             "dtype": f"f{args.precision}", "data": "synthetic",
             "config": workload_config(args, wl), "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches,
-            "clocks": clk.summary(), "fp64": fp64, "batch": batch,
+            "clocks": clk.summary(), "fp64": fp64, "batch": batch, "warm_start": warm,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

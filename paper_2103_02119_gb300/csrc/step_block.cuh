@@ -491,7 +491,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                     }
                 }
             }
-            if (p.moving) {
+            if (p.moving && (edge_row || has_first || has_last)) {
 #pragma unroll
                 for (int j = 0; j < VC; ++j) {
                     const int cx = xa + j;

@@ -107,3 +107,54 @@ def test_shallow_cavity_square_vs_rectangular():
     x_rc = (np.arange(100) + 0.5) / 100
     inside = (x_sq >= x_rc[0]) & (x_sq <= x_rc[-1])   # no extrapolation
     assert np.abs(np.interp(x_sq, x_rc, v_rc) - v_sq)[inside].max() < 0.02
+
+
+def _amplitude(u, phase_field):
+    """FP64 projection of a velocity component onto sin(phase)."""
+    s = np.sin(phase_field)
+    return float((u * s).sum() / (s * s).sum())
+
+
+@pytest.mark.parametrize("a", [0.25, 0.5, 1.0])
+@pytest.mark.parametrize("nu", [1e-3, 1e-2])
+def test_config2_shear_wave_decay_rates(a, nu):
+    """Config 2 at full size (2048 x 1024, periodic, lambda = 256 dx, u0 = 0.02,
+    10,000 steps, FP32): the x- and the y-varying shear wave decay at the
+    closed-form rate nu k^2 (within 1 % at nu = 1e-2, 3 % at nu = 1e-3) and
+    at rates equal to each other (the isotropy the corrections restore)."""
+    cs2 = W.stable_cs2(a)
+    rates = {}
+    for direction in ("y", "x"):
+        wl = W.shear_wave(2048, 1024, a, cs2, nu, direction, u0=0.02, seed=3, wavelength=256)
+        g = lattice(wl, 32)
+        k = wl.info["k"]
+        x, y = W.coords(wl.nx, wl.ny, a)
+        ph = (k * y if direction == "y" else k * x) + wl.info["phase"]
+        ts, amps = [], []
+        for n in range(0, 10001, 2000):
+            if n:
+                g.step(2000)
+            _, u, v = g.moments()
+            amps.append(_amplitude(u if direction == "y" else v, ph))
+            ts.append(n)
+        rate = -np.polyfit(ts, np.log(amps), 1)[0]
+        rates[direction] = rate
+        tol = 0.01 if nu >= 1e-2 else 0.03
+        assert abs(rate / (nu * k * k) - 1.0) < tol, (direction, rate, nu * k * k)
+        g.close()
+    assert abs(rates["x"] / rates["y"] - 1.0) < (0.005 if nu >= 1e-2 else 0.015), rates
+
+
+def test_config2_fp32_tracks_fp64_over_10000_steps():
+    """Config 2: a Taylor-Green field at a = 0.5, nu = 1e-2 over 10,000 steps;
+    the FP32 deviation storage stays within 1e-5 (relative L2 on u) of the
+    FP64 run, which is itself parity-tested against the FP64 oracle."""
+    wl = W.taylor_green(2048, 1024, 0.5, W.stable_cs2(0.5), 1e-2, u0=0.02, seed=4,
+                        wavelength=256)
+    g32, g64 = lattice(wl, 32), lattice(wl, 64)
+    g32.step(10000)
+    g64.step(10000)
+    _, u32, v32 = g32.moments()
+    _, u64, v64 = g64.moments()
+    err = float(np.sqrt(((u32 - u64) ** 2 + (v32 - v64) ** 2).sum() / (u64 ** 2 + v64 ** 2).sum()))
+    assert err <= 1e-5, err

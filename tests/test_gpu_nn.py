@@ -89,3 +89,55 @@ def test_batch_size_limits():
     with pytest.raises(L.LbmError):
         L.lbm_nn_forward(nn, np.zeros((3, 8, 8, 4), np.float32))
     L.lbm_nn_destroy(nn)
+
+
+def test_warm_start_against_rest_start(orc):
+    """A network trained on solver-generated steady cavities starts new
+    instances; the unmodified scheme finishes them to the same residual.  The
+    warm-started final fields equal the rest-started ones (the same steady
+    state), and stay steady under the FP64 oracle.  The steps either way are
+    reported (the gain is not asserted: it depends on the prediction error,
+    see the design notes)."""
+    from paper_2103_02119_gb300 import warmstart as WS
+    n = 32
+    wls, x, t, fl, _ = WS.build_dataset(128, seed=0, n=n, max_steps=200_000)
+    assert len(wls) >= 120
+    ws = WS.WarmStart([16, 32, 64, 128], n=n, max_batch=32, seed=0)
+    hist = ws.train(x, t, fl, epochs=20, lr=2e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    test = WS.cavity_set(8, seed=1, n=n)
+    y = ws.predict(WS.inputs_of(test))
+    assert np.isfinite(y).all()
+    rest = WS.solve(test, max_steps=200_000)
+    warm = WS.solve(test, inits=[WS.fields_of(w, y[k]) for k, w in enumerate(test)],
+                    max_steps=400_000)
+    for res in (rest, warm):
+        assert np.all((res["residual"] >= 0) & (res["residual"] <= 1e-8))
+    print("steps rest", rest["steps"].tolist(), "warm", warm["steps"].tolist())
+    # both stop within the residual's reach of the steady state, and the
+    # warm start carries the prediction's total mass (the pressure level),
+    # so the two agree to a small fraction of the lid speed, not to rounding
+    for k, w in enumerate(test):
+        fluid = w.mask == 0
+        U = w.info["U"]
+        for a, b in zip(rest["fields"][k][1:], warm["fields"][k][1:]):
+            assert np.abs(a - b)[fluid].max() < 5e-3 * U
+    # the warm-started steady state of one instance under the FP64 oracle
+    from paper_2103_02119_gb300.lbm import Batch
+    w = test[0]
+    b = Batch([w])
+    b.init_fields(0, *WS.fields_of(w, y[0]))
+    b.run(1e-8, check_every=100, max_steps=400_000)
+    f = b.get_f(0)
+    _, ug, vg = b.moments(0)
+    b.close()
+    p = orc.OracleParams.make(w.nx, w.ny, w.a, w.cs2, w.omega, periodic_x=0, periodic_y=0,
+                              wall_u=w.wall_u)
+    o = orc.Oracle(p, w.mask)
+    o.set_f(f)
+    o.step(200)
+    _, uo, vo = o.moments()
+    fluid = o.solid() == 0
+    assert np.abs(uo - ug)[fluid].max() < 1e-3 * w.info["U"]
+    assert np.abs(vo - vg)[fluid].max() < 1e-3 * w.info["U"]
+    ws.close()
