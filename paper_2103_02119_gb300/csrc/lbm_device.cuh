@@ -177,27 +177,34 @@ __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
                                                        typename Lane<T>::V dxr,
                                                        typename Lane<T>::V dyr) {
     using V = typename Lane<T>::V;
-    const V rho = vadd(c.rho0, d);
-    const V jx = vsub(vadd(vadd(f[1], f[5]), f[8]), vadd(vadd(f[3], f[6]), f[7]));
-    const V jy = vmul(c.a, vsub(vadd(vadd(f[2], f[5]), f[6]), vadd(vadd(f[4], f[7]), f[8])));
-    const V ir = vrcp(rho);
-    const V ux = vmul(vadd(jx, c.hFx), ir);
-    const V uy = vmul(vadd(jy, c.hFy), ir);
-    const V nux = vneg(ux), nuy = vneg(uy);
-
-    // Central moments along y of each column e_x = 0, +1, -1:
-    // k0 = sum g, k1 = sum g (e_y - u_y), k2 = sum g (e_y - u_y)^2.
-    V k0[3], k1[3], k2[3];
+    // Column sums of each column e_x = 0, +1, -1: sq = g(+a) + g(-a),
+    // ad = a (g(+a) - g(-a)), k0 = g(0) + sq; the momentum is
+    // j = (k0(+1) - k0(-1), ad(0) + ad(+1) + ad(-1)).
+    V sq[3], ad[3], k0[3], k1[3], k2[3];
     {
         const V gz[3] = {f[0], f[1], f[3]}, gp[3] = {f[2], f[5], f[6]},
                 gm[3] = {f[4], f[8], f[7]};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            const V s = vadd(gp[q], gm[q]), dd = vsub(gp[q], gm[q]);
-            k0[q] = vadd(gz[q], s);
-            k1[q] = vfma(nuy, k0[q], vmul(c.a, dd));
-            k2[q] = vfma(nuy, vfma(c.a, dd, k1[q]), vmul(c.a2, s));
+            sq[q] = vadd(gp[q], gm[q]);
+            ad[q] = vmul(c.a, vsub(gp[q], gm[q]));
+            k0[q] = vadd(gz[q], sq[q]);
         }
+    }
+    const V rho = vadd(c.rho0, d);
+    const V jx = vsub(k0[1], k0[2]);
+    const V jy = vadd(vadd(ad[0], ad[1]), ad[2]);
+    const V ir = vrcp(rho);
+    const V ux = vmul(vadd(jx, c.hFx), ir);
+    const V uy = vmul(vadd(jy, c.hFy), ir);
+    const V nux = vneg(ux), nuy = vneg(uy);
+
+    // Central moments along y of each column:
+    // k0 = sum g, k1 = sum g (e_y - u_y), k2 = sum g (e_y - u_y)^2.
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        k1[q] = vfma(nuy, k0[q], ad[q]);
+        k2[q] = vfma(nuy, vadd(ad[q], k1[q]), vmul(c.a2, sq[q]));
     }
     // Along x: C[p][q] = sum_X (e_x - u_x)^p k_q(X).
     V C[3][3];
@@ -306,15 +313,9 @@ __device__ __forceinline__ typename Lane<T>::V collide_raw(const CollConst<T>& c
                                                            typename Lane<T>::V dxr,
                                                            typename Lane<T>::V dyr) {
     using V = typename Lane<T>::V;
-    const V rho = vadd(c.rho0, d);
-    const V jx = vsub(vadd(vadd(f[1], f[5]), f[8]), vadd(vadd(f[3], f[6]), f[7]));
-    const V jy = vmul(c.a, vsub(vadd(vadd(f[2], f[5]), f[6]), vadd(vadd(f[4], f[7]), f[8])));
-    const V ir = vrcp(rho);
-    const V ux = vmul(vadd(jx, c.hFx), ir);
-    const V uy = vmul(vadd(jy, c.hFy), ir);
-
     // Raw moments along y of each column: k0 = sum g, k1 = sum g e_y,
-    // k2 = sum g e_y^2; then along x: R[p][q] = sum_X e_x^p k_q(X).
+    // k2 = sum g e_y^2; then along x: R[p][q] = sum_X e_x^p k_q(X).  The
+    // momentum is j = (k0(+1) - k0(-1), k1(0) + k1(+1) + k1(-1)).
     V k0[3], k1[3], k2[3];
     {
         const V gz[3] = {f[0], f[1], f[3]}, gp[3] = {f[2], f[5], f[6]},
@@ -327,6 +328,12 @@ __device__ __forceinline__ typename Lane<T>::V collide_raw(const CollConst<T>& c
             k2[q] = vmul(c.a2, s);
         }
     }
+    const V rho = vadd(c.rho0, d);
+    const V jx = vsub(k0[1], k0[2]);
+    const V jy = vadd(vadd(k1[0], k1[1]), k1[2]);
+    const V ir = vrcp(rho);
+    const V ux = vmul(vadd(jx, c.hFx), ir);
+    const V uy = vmul(vadd(jy, c.hFy), ir);
     V R[3][3];
     {
         const V* kq[3] = {k0, k1, k2};

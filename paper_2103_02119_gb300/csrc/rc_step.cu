@@ -11,6 +11,8 @@ namespace lbm {
 // lattice whose block range [begin, begin + nseg * nbands) holds w.  The
 // lattice's parameters are copied from the (read-only) lattice table into
 // shared memory for the item, so the collision reads its constants there.
+// (No minimum of blocks per SM: the lattice parameters read from shared
+// memory raise the register need; measured faster unbounded.)
 template <typename T, int BXT, int SCH>
 __global__ void __launch_bounds__(BXT)
 rc_batch_kernel(const BatchLattice<T>* __restrict__ lat, const int* __restrict__ active,

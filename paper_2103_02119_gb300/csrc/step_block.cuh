@@ -17,22 +17,23 @@
 // Staging.  The populations a row pulls (plane i of the source row
 // y - e_iy, columns x0-4 .. x0+W+3) are brought into shared memory by TMA
 // bulk copies (cp.async.bulk, completion counted on an mbarrier), issued by
-// lanes of warp 0 one row ahead into a three-stage ring.  A thread reads its cells'
-// nine populations with vector shared loads (plus one scalar load for the
-// planes shifted along x).  Cells next to a wall or a solid, and the
+// lanes of warp 0 two rows ahead into a two-stage ring.  A thread reads its
+// cells' nine populations with vector shared loads (plus one scalar load for
+// the planes shifted along x) and keeps them in registers until the row
+// collides one iteration later, so a stage is free as soon as its row is read.  Cells next to a wall or a solid, and the
 // first/last column of a periodic axis, gather from global memory instead
 // (half-way bounce-back, wrap).  Results go out as vector global stores.
 //
 // Iteration k:
-//   1. wait for the stage of row k; sum each cell's nine populations into
-//      its density and put it into a four-row ring in shared memory (lanes of
-//      warp 0 add the density of the two columns just outside the segment,
-//      one population per lane);
+//   1. wait for the stage of row k; load each cell's nine populations into
+//      registers, sum them into its density and put it into a four-row ring
+//      in shared memory (lanes of warp 0 add the density of the two columns
+//      just outside the segment, one population per lane);
 //   2. one barrier (which also votes on a timed-out wait);
-//   3. warp 0 refills the stage freed by row k-2 with row k+1;
-//   4. row k-1 collides: its populations are read again from its stage, its
-//      density gradient comes from the ring by central differences (spacing 2
-//      along x, 2a along y; a wall or solid neighbour mirrors the cell's own
+//   3. warp 0 refills the stage of row k with row k+2;
+//   4. row k-1 collides from the populations kept in registers: its density
+//      gradient comes from the ring by central differences (spacing 2 along
+//      x, 2a along y; a wall or solid neighbour mirrors the cell's own
 //      density), and the result is stored to the cell's slot of the output.
 // The band includes one row before and after it, whose density the ring
 // needs.  Even bands march up and odd bands march down, so that two
@@ -49,7 +50,7 @@ namespace lbm {
 
 namespace {
 
-constexpr int kStages = 3;              // stage ring depth (copies run 1 row ahead)
+constexpr int kStages = 2;              // stage ring depth (copies run 2 rows ahead)
 constexpr int kHalo = 4;                // staged columns on each side of a segment
 constexpr unsigned kSpinLimit = 1u << 22;
 
@@ -220,6 +221,16 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     };
     // link bits of my VC cells in row rr (staged in stage s); returns their
     // OR (0: all fluid, no wall)
+    // Without a mask the bits split into a column part (west/east walls:
+    // bits 0, 4, 7 / 2, 5, 6) and a row part (south/north walls: bits 1, 4,
+    // 5 / 3, 6, 7); inactive cells are solid.
+    unsigned xbits[VC];
+#pragma unroll
+    for (int j = 0; j < VC; ++j) {
+        const int cx = xa + j;
+        const unsigned Wb = (cx == 0) & !p.px, Eb = (cx == p.nx - 1) & !p.px;
+        xbits[j] = (c0 + j < nseg) ? (Wb * 0x91u | Eb * 0x64u) : 0xFFu;
+    }
     auto cell_bits = [&](int s, int rr, unsigned* sb) -> unsigned {
         unsigned any = 0;
         if (MASK) {
@@ -231,13 +242,10 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
             }
         } else {
             const unsigned S = (rr == 0) & !p.py, N = (rr == p.ny - 1) & !p.py;
+            const unsigned ybits = S * 0x32u | N * 0xC8u;
 #pragma unroll
             for (int j = 0; j < VC; ++j) {
-                const int cx = xa + j;
-                const unsigned Wb = (cx == 0) & !p.px, Eb = (cx == p.nx - 1) & !p.px;
-                sb[j] = (c0 + j < nseg) ? (Wb | (S << 1) | (Eb << 2) | (N << 3) | ((Wb | S) << 4) |
-                                           ((Eb | S) << 5) | ((Eb | N) << 6) | ((Wb | N) << 7))
-                                        : 0xFFu;
+                sb[j] = xbits[j] | ybits;
                 any |= sb[j];
             }
         }
@@ -330,15 +338,20 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     }
     __syncthreads();
     if (tx < 32)
-        for (int k = 0; k < kStages - 2 && k < nit; ++k) issue(k);
+        for (int k = 0; k < kStages && k < nit; ++k) issue(k);
 
     unsigned sbp[VC];     // link bits of the previous row's cells
     bool fastp = false;   // its fast-path flag
     bool colp = false;    // whether it is collided
     int rrp = 0;          // its wrapped row index
     T dp[VC];             // its density deviations
+    T gp[9][VC];          // its populations
 #pragma unroll
     for (int j = 0; j < VC; ++j) { sbp[j] = 0xFFu; dp[j] = T(0); }
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j < VC; ++j) gp[i][j] = T(0);
 
     for (int k = 0; k < nit; ++k) {
         const int r = rfirst + dir * k;
@@ -353,12 +366,16 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         T dc[VC];
         bool fastc = false;
         bool colc = false;
+        T g[9][VC];
 #pragma unroll
         for (int j = 0; j < VC; ++j) { sbc[j] = 0xFFu; dc[j] = T(0); }
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+#pragma unroll
+            for (int j = 0; j < VC; ++j) g[i][j] = T(0);
         if (!to && rv && any_active) {
             const unsigned any = cell_bits(s, rr, sbc);
             fastc = xfast && any == 0u;
-            T g[9][VC];
             load(s, rr, sbc, fastc, g);
             if constexpr (sizeof(T) == 4) {  // both cells in one float2
                 float2 G[9];
@@ -414,24 +431,23 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         if (__syncthreads_or(to)) {
             if (tx == 0) {
                 atomicOr(p.status, 1);
-                // copies issued for iterations k .. k+kStages-3 may be in flight
-                for (int j = k; j < k + kStages - 2 && j < nit; ++j)
+                // copies issued for iterations k .. k+kStages-1 may be in flight
+                for (int j = k; j < k + kStages && j < nit; ++j)
                     mbar_wait(bar0 + 8u * (j % kStages), (unsigned)((j / kStages) & 1));
             }
             return false;
         }
 
-        // 3. refill the stage of row k-2 with row k+2
-        if (tx < 32 && k + kStages - 2 < nit) {
+        // 3. refill the stage of row k (now in registers) with row k+kStages
+        if (tx < 32 && k + kStages < nit) {
             fence_proxy_async();
-            issue(k + kStages - 2);
+            issue(k + kStages);
         }
 
         // 4. collide the previous row
         if (k >= 2 && colp) {
             const int rc = r - dir;
-            T g[9][VC];
-            load((k - 1) % kStages, rrp, sbp, fastp, g);
+            T (&gcol)[9][VC] = gp;
             const int sC = (k - 1) & 3;
             const int sN = dir > 0 ? (k & 3) : ((k - 2) & 3);
             const int sS = dir > 0 ? ((k - 2) & 3) : (k & 3);
@@ -463,7 +479,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                     static_assert(VC == 2, "FP32 collides its two cells as one float2");
                     float2 F[9];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) F[i] = make_float2(g[i][0], g[i][1]);
+                    for (int i = 0; i < 9; ++i) F[i] = make_float2(gcol[i][0], gcol[i][1]);
                     const float2 D = make_float2(dp[0], dp[1]);
                     const float2 Gx = make_float2(dxr[0], dxr[1]), Gy = make_float2(dyr[0], dyr[1]);
                     const float2 R = (SCH == 1 || (SCH == 2 && p.raw))
@@ -473,8 +489,8 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                     rho[1] = R.y;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        if (sbp[0] != 0xFFu) g[i][0] = F[i].x;
-                        if (sbp[1] != 0xFFu) g[i][1] = F[i].y;
+                        if (sbp[0] != 0xFFu) gcol[i][0] = F[i].x;
+                        if (sbp[1] != 0xFFu) gcol[i][1] = F[i].y;
                     }
                 } else {
 #pragma unroll
@@ -482,12 +498,12 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                         if (sbp[j] == 0xFFu) continue;
                         T F[9];
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) F[i] = g[i][j];
+                        for (int i = 0; i < 9; ++i) F[i] = gcol[i][j];
                         rho[j] = (SCH == 1 || (SCH == 2 && p.raw))
                                      ? collide_raw<T>(p.cc, F, dp[j], dxr[j], dyr[j])
                                      : collide<T>(p.cc, F, dp[j], dxr[j], dyr[j]);
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) g[i][j] = F[i];
+                        for (int i = 0; i < 9; ++i) gcol[i][j] = F[i];
                     }
                 }
             }
@@ -498,18 +514,22 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                     if (sbp[j] == 0xFFu || !(cx == 0 || cx == p.nx - 1 || edge_row)) continue;
                     T f[9];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) f[i] = g[i][j];
+                    for (int i = 0; i < 9; ++i) f[i] = gcol[i][j];
                     moving_wall(p, cx, rc, rho[j], f);
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) g[i][j] = f[i];
+                    for (int i = 0; i < 9; ++i) gcol[i][j] = f[i];
                 }
             }
             const I o = (I)rc * rs + xa;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) stv<T, VC>(fout + (i * pl + o), g[i]);
+            for (int i = 0; i < 9; ++i) stv<T, VC>(fout + (i * pl + o), gcol[i]);
         }
 #pragma unroll
         for (int j = 0; j < VC; ++j) { sbp[j] = sbc[j]; dp[j] = dc[j]; }
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+#pragma unroll
+            for (int j = 0; j < VC; ++j) gp[i][j] = g[i][j];
         fastp = fastc;
         colp = colc;
         rrp = rr;
@@ -523,12 +543,12 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     return true;
 }
 
-// Blocks per SM the register allocator is asked to fit (80 registers a
-// thread in FP32): FP32 at 128 threads is limited to 6 blocks by its shared
-// memory, so registers should allow 6; narrower blocks scale with it.
+// Blocks per SM the register allocator is asked to fit: in FP32 about 100
+// registers a thread (the collision plus the populations kept from the
+// previous row), narrower blocks scaling with it; in FP64 three blocks of 128.
 template <typename T>
 constexpr int step_min_blocks(int bxt) {
-    return sizeof(T) != 4 ? 1 : bxt == 128 ? 6 : bxt == 64 ? 12 : bxt == 32 ? 24 : 1;
+    return sizeof(T) != 4 ? (bxt == 128 ? 3 : 1) : bxt == 128 ? 5 : bxt == 64 ? 10 : bxt == 32 ? 20 : 1;
 }
 
 template <typename T, bool MASK, int BXT, typename I, int SCH>

@@ -96,3 +96,28 @@ def max_reynolds(grids=((100, 200), (200, 400), (300, 600)), a=0.5, U=0.2, cs2=0
             b = Re
         best[key] = b
     return best
+
+
+def main(argv=None):
+    """python -m paper_2103_02119_gb300.stability [--steps N] [--table6-grids G]
+    prints the two sweeps as JSON lines."""
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=100_000)
+    ap.add_argument("--table6-grids", default="100x200,200x400,300x600")
+    args = ap.parse_args(argv)
+    thr = lid_velocity_thresholds(steps=args.steps)
+    print(json.dumps({"fig17_max_lid_speed": [
+        {"a": a, "tau": tau, "scheme": "RC" if sc == 0 else "RNR", "U_max": u}
+        for (a, tau, sc), u in sorted(thr.items())], "steps": args.steps}), flush=True)
+    grids = [tuple(int(v) for v in g.split("x")) for g in args.table6_grids.split(",") if g]
+    best = max_reynolds(grids=grids, steps=args.steps)
+    print(json.dumps({"table6_max_re": [
+        {"grid": f"{nx}x{ny}", "scheme": "RC" if sc == 0 else "RNR", "Re_max": r}
+        for (nx, ny, sc), r in sorted(best.items())], "steps": args.steps}), flush=True)
+
+
+if __name__ == "__main__":
+    main()
