@@ -336,6 +336,36 @@ def batch_time_to_residual(torch, count, max_steps, tol=1e-8, check=100):
             "sequential_max_steps": max(steps_s), "speedup": ts / tb}
 
 
+# ------------------------------------------------------------ small lattice --
+
+def small_lattice(torch):
+    """Config 1 (Poiseuille channel, 32 x 32, a = 0.5, FP64, 5,000 steps):
+    a lattice this small is bound by launch latency; lbm_step replays runs
+    of 50 steps from a CUDA graph, against one call per step."""
+    from paper_2103_02119_gb300 import workloads as W
+    from paper_2103_02119_gb300.lbm import Lattice
+    stream = torch.cuda.current_stream()
+    wl = W.poiseuille(ny=32, nx=32, a=0.5, cs2=0.16, nu=0.1, U=0.01)
+    out = {"workload": "Poiseuille channel 32x32, a=0.5, nu=0.1, FP64", "steps": 5000}
+    for mode in ("graph", "per_call"):
+        lat = Lattice.from_workload(wl, precision=64, stream=stream)
+        lat.step(100)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if mode == "graph":
+            lat.step(5000)
+        else:
+            for _ in range(5000):
+                lat.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[f"{mode}_us_per_step"] = e0.elapsed_time(e1) * 1e3 / 5000
+        lat.close()
+    return out
+
+
 # ---------------------------------------------------------------- warm start --
 
 def warm_start_measure(torch, ntrain, epochs, n=32, ntest=32):
@@ -493,6 +523,8 @@ def main():
         batch["time_to_residual"] = batch_time_to_residual(torch, args.ttr_count,
                                                            args.ttr_max_steps)
 
+    small = small_lattice(torch) if rank == 0 and not args.no_batch else None
+
     warm = None
     if rank == 0 and not args.no_warm:
         warm = warm_start_measure(torch, args.warm_train, args.warm_epochs)
@@ -511,7 +543,8 @@ def main():
             "dtype": f"f{args.precision}", "data": "synthetic",
             "config": workload_config(args, wl), "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches,
-            "clocks": clk.summary(), "fp64": fp64, "batch": batch, "warm_start": warm,
+            "clocks": clk.summary(), "fp64": fp64, "batch": batch, "small_lattice": small,
+            "warm_start": warm,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -118,8 +118,10 @@ void lbm_destroy(lbm_handle* h);
 lbm_status lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
                            const double* uy, int on_device);
 
-/* Advance nsteps >= 0 time steps (collide + stream, Sec. 4).  Asynchronous:
- * the return value reports launch errors only. */
+/* Advance nsteps >= 0 time steps (collide + stream, Sec. 4), one kernel
+ * launch per step; runs of 50 steps replay a CUDA graph the handle captures
+ * once per starting buffer (on a stream of its own; lbm_set_force drops
+ * it).  Asynchronous: the return value reports launch errors only. */
 lbm_status lbm_step(lbm_handle* h, int64_t nsteps);
 
 /* Replace the uniform body force (takes effect from the next step). */

@@ -44,6 +44,8 @@ struct lbm_handle {
     int diag_blocks = 0;
     int bx = 0, nbands = 0;
     int64_t steps = 0, launches = 0;
+    cudaStream_t cap = nullptr;                     // owned, for graph capture only
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // runs of steps from f[0] / f[1]
     char err[512] = {0};
     unsigned long long serial = next_handle_serial();
 };
@@ -318,6 +320,69 @@ lbm_status device_inputs(lbm_handle* h, const double* const* in, int n, int on_d
     return LBM_OK;
 }
 
+// Steps per captured graph of a single lattice (even, so a run starts and
+// ends on the same buffer).
+constexpr int kRunSteps = 50;
+
+void drop_run_graphs(lbm_handle* h) {
+    for (auto& g : h->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// Launches n steps from buffer `from` on stream s.
+template <typename T>
+cudaError_t launch_steps_of(lbm_handle* h, const KParams<T>& k, int from, int n, cudaStream_t s) {
+    for (int i = 0; i < n; ++i) {
+        const int c = (from + i) & 1;
+        cudaError_t e = lbm::launch_step<T>((const T*)h->f[c], (T*)h->f[c ^ 1], k, h->bx,
+                                            h->nbands, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// The graph of kRunSteps steps starting from buffer `from`, captured once
+// on the handle's own stream (the parameters are fixed in it; changing them
+// drops the graphs).
+template <typename T>
+lbm_status ensure_run_graph(lbm_handle* h, const KParams<T>& k, int from) {
+    if (h->graph[from]) return LBM_OK;
+    if (!h->cap) CK(h, cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+    cudaError_t e = launch_steps_of<T>(h, k, from, kRunSteps, h->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h, e != cudaSuccess ? e : e2, "graph capture of the step");
+    }
+    e = cudaGraphInstantiate(&h->graph[from], g, 0);
+    cudaGraphDestroy(g);
+    CK(h, e, "cudaGraphInstantiate");
+    return LBM_OK;
+}
+
+template <typename T>
+lbm_status step_lattice(lbm_handle* h, int64_t nsteps) {
+    const KParams<T> k = kparams<T>(h);
+    int64_t left = nsteps;
+    while (left >= kRunSteps) {
+        if (lbm_status st = ensure_run_graph<T>(h, k, h->cur); st != LBM_OK) return st;
+        CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream), "cudaGraphLaunch");
+        left -= kRunSteps;
+        h->launches += kRunSteps;
+        h->steps += kRunSteps;
+    }
+    CK(h, launch_steps_of<T>(h, k, h->cur, (int)left, h->stream), "step kernel");
+    h->cur ^= (int)(left & 1);
+    h->launches += left;
+    h->steps += left;
+    return LBM_OK;
+}
+
 void reset_counters(lbm_handle* h) {
     h->steps = 0;
     h->have_prev = 0;
@@ -439,6 +504,8 @@ lbm_status lbm_create(const lbm_params* p, const uint8_t* solid_mask, void* cuda
 
 void lbm_destroy(lbm_handle* h) {
     if (!h) return;
+    drop_run_graphs(h);
+    if (h->cap) cudaStreamDestroy(h->cap);
     if (h->f[0]) cudaFree(h->f[0]);
     if (h->f[1]) cudaFree(h->f[1]);
     if (h->lmask) cudaFree(h->lmask);
@@ -472,26 +539,12 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
         set_err(h, "nsteps must be >= 0");
         return LBM_ERR_INVALID;
     }
-    if (h->p.precision == 64) {
-        const KParams<double> k = kparams<double>(h);
-        for (int64_t n = 0; n < nsteps; ++n) {
-            CK(h, lbm::launch_step<double>((const double*)h->f[h->cur], (double*)h->f[h->cur ^ 1],
-                                           k, h->bx, h->nbands, h->stream),
-               "step kernel");
-            h->cur ^= 1;
-            ++h->launches;
-            ++h->steps;
-        }
-    } else {
-        const KParams<float> k = kparams<float>(h);
-        for (int64_t n = 0; n < nsteps; ++n) {
-            CK(h, lbm::launch_step<float>((const float*)h->f[h->cur], (float*)h->f[h->cur ^ 1],
-                                          k, h->bx, h->nbands, h->stream),
-               "step kernel");
-            h->cur ^= 1;
-            ++h->launches;
-            ++h->steps;
-        }
+    // runs of kRunSteps steps replay a captured graph, the rest launch directly
+    while (nsteps > 0) {
+        const int64_t n = nsteps < (1LL << 30) ? nsteps : (1LL << 30);
+        lbm_status st = h->p.precision == 64 ? step_lattice<double>(h, n) : step_lattice<float>(h, n);
+        if (st != LBM_OK) return st;
+        nsteps -= n;
     }
     return LBM_OK;
 }
@@ -504,6 +557,7 @@ lbm_status lbm_set_force(lbm_handle* h, double Fx, double Fy) {
     }
     h->p.Fx = Fx;
     h->p.Fy = Fy;
+    drop_run_graphs(h);  // the captured steps carry the old force
     return LBM_OK;
 }
 
