@@ -484,12 +484,15 @@ lbm_status lbm_create(const lbm_params* p, const uint8_t* solid_mask, void* cuda
     if (nb == 0) {
         // Short bands (about 14 rows) keep the blocks that run at the same
         // time on nearby rows; enough of them to fill every SM, but bands of
-        // at least 6 rows so that the two extra rows a band reads stay cheap.
+        // at least 6 rows so that the two extra rows a band reads stay cheap
+        // -- unless even that leaves SMs idle (small lattices, whose step
+        // time is one block's row march): then bands down to one row.
         const int occ = p->precision == 64 ? lbm::step_occupancy<double>(bx, solid_mask != nullptr)
                                            : lbm::step_occupancy<float>(bx, solid_mask != nullptr);
         const int fill = (occ * sms + nseg - 1) / nseg;
+        const int cap = (long long)nseg * (p->ny / 6) >= sms ? p->ny / 6 : p->ny;
         nb = p->ny / 14;
-        if (nb < fill) nb = fill < p->ny / 6 ? fill : p->ny / 6;
+        if (nb < fill) nb = fill < cap ? fill : cap;
         if (nb < 1) nb = 1;
     }
     if (nb > p->ny) nb = p->ny;
