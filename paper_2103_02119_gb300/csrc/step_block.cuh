@@ -17,7 +17,7 @@
 // Staging.  The populations a row pulls (plane i of the source row
 // y - e_iy, columns x0-4 .. x0+W+3) are brought into shared memory by TMA
 // bulk copies (cp.async.bulk, completion counted on an mbarrier), issued by
-// lanes of warp 0 two rows ahead into a two-stage ring.  A thread reads its
+// lanes of one warp two rows ahead into a two-stage ring.  A thread reads its
 // cells' nine populations with vector shared loads (plus one scalar load for
 // the planes shifted along x) and keeps them in registers until the row
 // collides one iteration later, so a stage is free as soon as its row is read.  Cells next to a wall or a solid, and the
@@ -30,7 +30,7 @@
 //      in shared memory (lanes of the last warp add the density of the two columns
 //      just outside the segment, one population per lane);
 //   2. one barrier (which also votes on a timed-out wait);
-//   3. warp 0 refills the stage of row k with row k+2;
+//   3. the issuing warp refills the stage of row k with row k+2;
 //   4. row k-1 collides from the populations kept in registers: its density
 //      gradient comes from the ring by central differences (spacing 2 along
 //      x, 2a along y; a wall or solid neighbour mirrors the cell's own
@@ -166,6 +166,10 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
 
     const int tx = threadIdx.x;
     const int lane = tx & 31;
+    // the warp that issues the copies: warp 1 of four, not the last warp,
+    // which adds the halo densities (the per-row barrier waits on the
+    // slowest warp)
+    constexpr int kIssueWarp = BXT >= 128 ? 1 : 0;
     const int x0 = seg * W;
     const int nseg = min(W, p.nx - x0);
     const int c0 = VC * tx;              // first cell of this thread, within the segment
@@ -196,8 +200,8 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     // periodic edge column, and (per row) none has a wall or solid source
     const bool xfast = all_active && !(p.px && (has_first || has_last));
 
-    // halo lanes of the last warp (warp 0 issues the copies, so the extra
-    // work is split between two warps): lanes 0..8 take population `lane` of the column
+    // halo lanes of the last warp (another warp issues the copies, so the
+    // extra work is split between two warps): lanes 0..8 take population `lane` of the column
     // left of the segment, lanes 16..24 population `lane-16` of the column
     // right of it
     const int hside = lane >> 4, hi = lane & 15;
@@ -253,7 +257,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         return any;
     };
 
-    // warp 0: copies of the source rows of iteration k into its stage; lane 0
+    // the issuing warp: copies of the source rows of iteration k into its stage; lane 0
     // announces the byte count on the stage's mbarrier, lanes 0..8 copy one
     // plane each, lane 9 the row of the link mask (columns x0 .. x0 + mbytes;
     // x0 and the row pitch are multiples of 32, so the copy is 16-byte
@@ -338,7 +342,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         mbar_init_fence();
     }
     __syncthreads();
-    if (tx < 32)
+    if ((tx >> 5) == kIssueWarp)
         for (int k = 0; k < kStages && k < nit; ++k) issue(k);
 
     unsigned sbp[VC];     // link bits of the previous row's cells
@@ -440,7 +444,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         }
 
         // 3. refill the stage of row k (now in registers) with row k+kStages
-        if (tx < 32 && k + kStages < nit) {
+        if ((tx >> 5) == kIssueWarp && k + kStages < nit) {
             fence_proxy_async();
             issue(k + kStages);
         }
