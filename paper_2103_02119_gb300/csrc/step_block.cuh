@@ -27,7 +27,7 @@
 // Iteration k:
 //   1. wait for the stage of row k; load each cell's nine populations into
 //      registers, sum them into its density and put it into a four-row ring
-//      in shared memory (lanes of the last warp add the density of the two columns
+//      in shared memory (lanes of warp 0 add the density of the two columns
 //      just outside the segment, one population per lane);
 //   2. one barrier (which also votes on a timed-out wait);
 //   3. the issuing warp refills the stage of row k with row k+2;
@@ -166,9 +166,9 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
 
     const int tx = threadIdx.x;
     const int lane = tx & 31;
-    // the warp that issues the copies: warp 1 of four, not the last warp,
-    // which adds the halo densities (the per-row barrier waits on the
-    // slowest warp)
+    // the warp that issues the copies: warp 1 of four, not warp 0, which
+    // adds the halo densities (the per-row barrier waits on the slowest
+    // warp)
     constexpr int kIssueWarp = BXT >= 128 ? 1 : 0;
     const int x0 = seg * W;
     const int nseg = min(W, p.nx - x0);
@@ -200,12 +200,12 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     // periodic edge column, and (per row) none has a wall or solid source
     const bool xfast = all_active && !(p.px && (has_first || has_last));
 
-    // halo lanes of the last warp (another warp issues the copies, so the
-    // extra work is split between two warps): lanes 0..8 take population `lane` of the column
+    // halo lanes of warp 0 (another warp issues the copies, so the extra
+    // work is split between two warps): lanes 0..8 take population `lane` of the column
     // left of the segment, lanes 16..24 population `lane-16` of the column
     // right of it
     const int hside = lane >> 4, hi = lane & 15;
-    const bool hlane = tx >= BXT - 32 && hi < 9;
+    const bool hlane = tx < 32 && hi < 9;
     const int hraw = hside == 0 ? x0 - 1 : x0 + nseg;
     int hx = hraw;
     bool hok = true;
@@ -406,7 +406,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
             for (int j = 0; j < VC; ++j)
                 if (c0 + j < nseg) ring[slot * RW + c0 + 4 + j] = dc[j];
         }
-        if (tx >= BXT - 32) {
+        if (tx < 32) {
             T h = T(0);
             if (!to && rv && hpull) {
                 const unsigned hb = bits_at(hx, rr);

@@ -22,8 +22,9 @@ import numpy as np
 from . import workloads as W
 
 
-def fig17_cs2(a: float) -> float:
-    return min(1.0 / 3.0, 0.6 * a * a)
+def fig17_cs2(a: float, factor: float = 0.6) -> float:
+    """c_s^2 of the lid-speed sweep: min(1/3, factor a^2)."""
+    return min(1.0 / 3.0, factor * a * a)
 
 
 def _run(wls, schemes, steps, check, stream):
@@ -39,7 +40,8 @@ def _run(wls, schemes, steps, check, stream):
 
 
 def lid_velocity_thresholds(a_values=(1.0, 0.5, 0.3), taus=(0.51, 0.55, 0.6, 0.7, 0.8, 1.0),
-                            u_values=None, steps=100_000, check=1000, nx=21, stream=None):
+                            u_values=None, steps=100_000, check=1000, nx=21, stream=None,
+                            cs2_factor=0.6):
     """Returns {(a, tau, scheme): largest U of u_values such that it and
     every smaller U stayed stable}; scheme 0 = RC-LBM, 1 = RNR-LBM."""
     if u_values is None:
@@ -47,7 +49,7 @@ def lid_velocity_thresholds(a_values=(1.0, 0.5, 0.3), taus=(0.51, 0.55, 0.6, 0.7
     wls, schemes, keys = [], [], []
     for a in a_values:
         ny = int(round((nx - 1) / a)) + 1
-        cs2 = fig17_cs2(a)
+        cs2 = fig17_cs2(a, cs2_factor)
         for tau in taus:
             nu = cs2 * (tau - 0.5)
             for U in u_values:
@@ -107,11 +109,14 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=100_000)
     ap.add_argument("--table6-grids", default="100x200,200x400,300x600")
+    ap.add_argument("--cs2-factor", type=float, default=0.6,
+                    help="c_s^2 = min(1/3, factor a^2) in the lid-speed sweep")
     args = ap.parse_args(argv)
-    thr = lid_velocity_thresholds(steps=args.steps)
+    thr = lid_velocity_thresholds(steps=args.steps, cs2_factor=args.cs2_factor)
     print(json.dumps({"fig17_max_lid_speed": [
         {"a": a, "tau": tau, "scheme": "RC" if sc == 0 else "RNR", "U_max": u}
-        for (a, tau, sc), u in sorted(thr.items())], "steps": args.steps}), flush=True)
+        for (a, tau, sc), u in sorted(thr.items())], "steps": args.steps,
+        "cs2_factor": args.cs2_factor}), flush=True)
     grids = [tuple(int(v) for v in g.split("x")) for g in args.table6_grids.split(",") if g]
     best = max_reynolds(grids=grids, steps=args.steps)
     print(json.dumps({"table6_max_re": [
