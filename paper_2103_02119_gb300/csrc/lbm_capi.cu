@@ -606,13 +606,13 @@ lbm_status lbm_stress(lbm_handle* h, double* dxux, double* dyuy, double* sxy, do
     cudaError_t e;
     if (h->p.precision == 64) {
         e = lbm::launch_moments<double>((const double*)h->f[h->cur], a, rho, nullptr, nullptr,
-                                        h->stream);
+                                        h->stream, true);
         if (e == cudaSuccess)
             e = lbm::launch_stress<double>((const double*)h->f[h->cur], a, rho, d[0], d[1], d[2],
                                            d[3], d[4], d[5], h->stream);
     } else {
         e = lbm::launch_moments<float>((const float*)h->f[h->cur], a, rho, nullptr, nullptr,
-                                       h->stream);
+                                       h->stream, true);
         if (e == cudaSuccess)
             e = lbm::launch_stress<float>((const float*)h->f[h->cur], a, rho, d[0], d[1], d[2],
                                           d[3], d[4], d[5], h->stream);

@@ -80,9 +80,11 @@ cudaError_t launch_set_f(T* f, const AuxParams& p, const double* fin, cudaStream
 // post-stream distributions / moments of the state (device outputs)
 template <typename T>
 cudaError_t launch_get_f(const T* f, const AuxParams& p, double* fout, cudaStream_t s);
+// exact64: rho and u in FP64 arithmetic (diagnostics, stress); otherwise FP32
+// storage is read out in FP32 (rho = rho0 + d still in FP64).
 template <typename T>
 cudaError_t launch_moments(const T* f, const AuxParams& p, double* rho, double* ux,
-                           double* uy, cudaStream_t s);
+                           double* uy, cudaStream_t s, bool exact64 = false);
 // Local strain rates and viscous stress (FP64, nullable outputs of nx*ny
 // doubles) of the state; rho: the density field of the same state (from
 // launch_moments).

@@ -30,17 +30,49 @@ __device__ __forceinline__ long long target(const AuxParams& p, int x, int y, in
     return (long long)ty * p.nx + tx;
 }
 
-template <typename T, bool MASK>
-__global__ void init_kernel(T* __restrict__ f, const AuxParams p, const double* rho,
+// f_i^eq(r, u, v) - w_i rho0, the stored deviation of an equilibrium.  FP64
+// storage evaluates f^eq in FP64 and subtracts the rest part.
+__device__ __forceinline__ double feq_dev64(int i, double r, double u, double v,
+                                            const AuxParams& p) {
+    return feq_d(i, r, u, v, p.cs2, p.a) - p.wrest[i];
+}
+
+// FP32 storage carries the rest part analytically, as the step does: with
+// the 1-D factors X = X0 + dX (along x) and Y = Y0 + dY (along y), X0 Y0 =
+// w_i,
+//   r X Y - rho0 X0 Y0 = (r - rho0) X Y + rho0 (dX Y + X0 dY),
+// where dX, dY vanish with the velocity, so FP32 only forms small numbers
+// (and GB300's FP64 pipe, a small fraction of its FP32 rate, stays idle).
+// The state comes in FP32 too: dr = r - rho0, (u, v).
+struct Feq32 {
+    float cs2, a, iah2, rho0;
+    __device__ __forceinline__ float operator()(int i, float dr, float u, float v) const {
+        const int sx = ex(i), sy = ey(i);
+        const float X0 = sx == 0 ? 1.0f - cs2 : 0.5f * cs2;
+        const float dX = sx == 0 ? -u * u : 0.5f * (u * u + (float)sx * u);
+        const float Y0 = sy == 0 ? 1.0f - 2.0f * iah2 * cs2 : iah2 * cs2;
+        const float dY = sy == 0 ? -2.0f * iah2 * v * v : iah2 * (v * v + (float)sy * a * v);
+        const float X = X0 + dX, Y = Y0 + dY;
+        return dr * X * Y + rho0 * (dX * Y + X0 * dY);
+    }
+};
+
+// One row per block row of the grid, x across the block: no division of a
+// cell index.
+#define LBM_FOR_CELLS(p)                                                                 \
+    for (int y = blockIdx.y; y < (p).ny; y += gridDim.y)                                 \
+        for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < (p).nx;                  \
+             x += gridDim.x * blockDim.x)
+
+template <bool MASK>
+__global__ void init_kernel(double* __restrict__ f, const AuxParams p, const double* rho,
                             const double* ux, const double* uy) {
-    const long long N = (long long)p.nx * p.ny;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % p.nx), y = (int)(c / p.nx);
+    LBM_FOR_CELLS(p) {
+        const long long c = (long long)y * p.nx + x;
         const long long o = (long long)y * p.rstride + x;
         const unsigned sb = link_bits<MASK>(p, x, y);
         if (sb == 0xFFu) {
-            for (int i = 0; i < 9; ++i) f[i * p.plane + o] = T(0);
+            for (int i = 0; i < 9; ++i) f[i * p.plane + o] = 0.0;
             continue;
         }
         const double r0 = rho ? rho[c] : 1.0, u0 = ux ? ux[c] : 0.0,
@@ -48,14 +80,87 @@ __global__ void init_kernel(T* __restrict__ f, const AuxParams p, const double* 
         for (int i = 0; i < 9; ++i) {
             double v;
             if (i > 0 && ((sb >> (opp(i) - 1)) & 1u)) {
-                v = feq_d(opp(i), r0, u0, v0, p.cs2, p.a);  // pulled back by c itself
+                v = feq_dev64(opp(i), r0, u0, v0, p);  // pulled back by c itself
             } else {
                 const long long t = i == 0 ? c : target(p, x, y, i);
-                v = feq_d(i, rho ? rho[t] : 1.0, ux ? ux[t] : 0.0, uy ? uy[t] : 0.0,
-                          p.cs2, p.a);
+                v = feq_dev64(i, rho ? rho[t] : 1.0, ux ? ux[t] : 0.0, uy ? uy[t] : 0.0, p);
             }
-            f[i * p.plane + o] = T(v - p.wrest[i]);
+            f[i * p.plane + o] = v;
         }
+    }
+}
+
+// FP32 storage: a block owns up to kThreads columns and marches down a band
+// of rows, keeping the FP32 state (r - rho0, u, v) of the rows y - 1, y,
+// y + 1 and of one column either side in shared memory, so that each cell's
+// FP64 input is converted once rather than once per population.
+constexpr int kInitRows = 16;  // rows of a band (more when ny / 16 > 65535)
+
+template <bool MASK>
+__global__ void __launch_bounds__(kThreads)
+init32_kernel(float* __restrict__ f, const AuxParams p, const double* rho, const double* ux,
+              const double* uy, int rows) {
+    constexpr int SW = kThreads + 2;
+    __shared__ float st[3][3][SW];  // [component][ring row][column x - x0 + 1]
+    const Feq32 feq{(float)p.cs2, (float)p.a, (float)(0.5 / (p.a * p.a)), (float)p.rho0};
+    const int tx = threadIdx.x;
+    const int x0 = blockIdx.x * kThreads;
+    const int w = min(kThreads, p.nx - x0);
+    const int y0 = blockIdx.y * rows;
+    const int y1 = min(p.ny, y0 + rows);
+    // ring slot of row yy in [y0 - 1, y1]
+    auto slot = [&](int yy) { return (yy - y0 + 1) % 3; };
+    auto load_row = [&](int yy) {
+        const int k = slot(yy);
+        int gy = yy;
+        if (gy < 0) gy = p.py ? gy + p.ny : -1;
+        else if (gy >= p.ny) gy = p.py ? gy - p.ny : -1;
+        for (int c = tx; c < w + 2; c += kThreads) {
+            int gx = x0 - 1 + c;
+            if (gx < 0) gx = p.px ? gx + p.nx : -1;
+            else if (gx >= p.nx) gx = p.px ? gx - p.nx : -1;
+            float dr = 0.0f, u = 0.0f, v = 0.0f;  // outside a wall: never read
+            if (gx >= 0 && gy >= 0) {
+                const long long t = (long long)gy * p.nx + gx;
+                dr = (float)((rho ? rho[t] : 1.0) - p.rho0);
+                u = ux ? (float)ux[t] : 0.0f;
+                v = uy ? (float)uy[t] : 0.0f;
+            }
+            st[0][k][c] = dr;
+            st[1][k][c] = u;
+            st[2][k][c] = v;
+        }
+    };
+    if (w <= 0 || y0 >= p.ny) return;
+    load_row(y0 - 1);
+    load_row(y0);
+    for (int y = y0; y < y1; ++y) {
+        load_row(y + 1);
+        __syncthreads();
+        if (tx < w) {
+            const int x = x0 + tx;
+            const long long o = (long long)y * p.rstride + x;
+            const unsigned sb = link_bits<MASK>(p, x, y);
+            if (sb == 0xFFu) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i * p.plane + o] = 0.0f;
+            } else {
+                const int k = slot(y), c = tx + 1;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    float v;
+                    if (i > 0 && ((sb >> (opp(i) - 1)) & 1u)) {
+                        // pulled back by the cell itself
+                        v = feq(opp(i), st[0][k][c], st[1][k][c], st[2][k][c]);
+                    } else {
+                        const int kk = slot(y + ey(i)), cc = c + ex(i);
+                        v = feq(i, st[0][kk][cc], st[1][kk][cc], st[2][kk][cc]);
+                    }
+                    f[i * p.plane + o] = v;
+                }
+            }
+        }
+        __syncthreads();  // row y - 1's slot is overwritten next
     }
 }
 
@@ -116,19 +221,41 @@ __device__ __forceinline__ void macro(const AuxParams& p, const T g[9], double& 
     uy = (p.a * jy + 0.5 * p.Fy) / rho;
 }
 
-template <typename T, bool MASK>
+// The read-out of FP32 storage (lbm_moments): the nine deviations summed in
+// FP32 and rho = rho0 + d formed in FP64, u in FP32 (the accuracy the FP32
+// state holds), so that the FP64 pipe only converts.  The diagnostics and
+// residuals keep the FP64 macro().
+__device__ __forceinline__ void macro_out(const AuxParams& p, const float g[9], double& rho,
+                                          double& ux, double& uy) {
+    float d = 0.0f, jx = 0.0f, jy = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        d += g[i];
+        if (ex(i) != 0) jx += ex(i) > 0 ? g[i] : -g[i];
+        if (ey(i) != 0) jy += ey(i) > 0 ? g[i] : -g[i];
+    }
+    rho = p.rho0 + (double)d;
+    const float r = (float)p.rho0 + d;
+    ux = (double)((jx + 0.5f * (float)p.Fx) / r);
+    uy = (double)(((float)p.a * jy + 0.5f * (float)p.Fy) / r);
+}
+__device__ __forceinline__ void macro_out(const AuxParams& p, const double g[9], double& rho,
+                                          double& ux, double& uy) {
+    macro(p, g, rho, ux, uy);
+}
+
+template <typename T, bool MASK, bool EXACT64>
 __global__ void moments_kernel(const T* __restrict__ f, const AuxParams p,
                                double* rho, double* ux, double* uy) {
-    const long long N = (long long)p.nx * p.ny;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % p.nx), y = (int)(c / p.nx);
+    LBM_FOR_CELLS(p) {
+        const long long c = (long long)y * p.nx + x;
         const unsigned sb = link_bits<MASK>(p, x, y);
         double r = 0.0, u = 0.0, v = 0.0;
         if (sb != 0xFFu) {
             T g[9];
             pull(f, p, x, y, sb, g);
-            macro(p, g, r, u, v);
+            if constexpr (EXACT64) macro(p, g, r, u, v);
+            else macro_out(p, g, r, u, v);
         }
         if (rho) rho[c] = r;
         if (ux) ux[c] = u;
@@ -415,14 +542,29 @@ int grid_for(long long N) {
     return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
 }
 
+// grid of LBM_FOR_CELLS: blocks across a row, rows down the grid, at most
+// 16384 blocks
+dim3 grid2_for(int nx, int ny) {
+    const int gx = (nx + kThreads - 1) / kThreads;
+    const int gy = ny < 16384 / gx ? ny : (16384 / gx > 0 ? 16384 / gx : 1);
+    return dim3(gx > 0 ? gx : 1, gy > 0 ? gy : 1);
+}
+
 }  // namespace
 
 template <typename T>
 cudaError_t launch_init(T* f, const AuxParams& p, const double* rho, const double* ux,
                         const double* uy, cudaStream_t s) {
-    const int g = grid_for((long long)p.nx * p.ny);
-    if (p.lmask) init_kernel<T, true><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy);
-    else init_kernel<T, false><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy);
+    if constexpr (sizeof(T) == 4) {
+        const int rows = max(kInitRows, (p.ny + 65534) / 65535);  // grid.y limit
+        const dim3 g((p.nx + kThreads - 1) / kThreads, (p.ny + rows - 1) / rows);
+        if (p.lmask) init32_kernel<true><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy, rows);
+        else init32_kernel<false><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy, rows);
+    } else {
+        const dim3 g = grid2_for(p.nx, p.ny);
+        if (p.lmask) init_kernel<true><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy);
+        else init_kernel<false><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy);
+    }
     return cudaGetLastError();
 }
 
@@ -444,10 +586,15 @@ cudaError_t launch_get_f(const T* f, const AuxParams& p, double* fout, cudaStrea
 
 template <typename T>
 cudaError_t launch_moments(const T* f, const AuxParams& p, double* rho, double* ux,
-                           double* uy, cudaStream_t s) {
-    const int g = grid_for((long long)p.nx * p.ny);
-    if (p.lmask) moments_kernel<T, true><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy);
-    else moments_kernel<T, false><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy);
+                           double* uy, cudaStream_t s, bool exact64) {
+    const dim3 g = grid2_for(p.nx, p.ny);
+    if (exact64) {
+        if (p.lmask) moments_kernel<T, true, true><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy);
+        else moments_kernel<T, false, true><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy);
+    } else {
+        if (p.lmask) moments_kernel<T, true, false><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy);
+        else moments_kernel<T, false, false><<<g, kThreads, 0, s>>>(f, p, rho, ux, uy);
+    }
     return cudaGetLastError();
 }
 
@@ -494,7 +641,7 @@ cudaError_t launch_batch_residual(const BatchLattice<float>* lat, const BatchAux
     template cudaError_t launch_get_f<T>(const T*, const AuxParams&, double*,         \
                                          cudaStream_t);                               \
     template cudaError_t launch_moments<T>(const T*, const AuxParams&, double*,       \
-                                           double*, double*, cudaStream_t);           \
+                                           double*, double*, cudaStream_t, bool);     \
     template cudaError_t launch_stress<T>(const T*, const AuxParams&, const double*,  \
                                           double*, double*, double*, double*, double*, \
                                           double*, cudaStream_t);                     \

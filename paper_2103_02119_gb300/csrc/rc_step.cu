@@ -11,10 +11,12 @@ namespace lbm {
 // lattice whose block range [begin, begin + nseg * nbands) holds w.  The
 // lattice's parameters are copied from the (read-only) lattice table into
 // shared memory for the item, so the collision reads its constants there.
-// (No minimum of blocks per SM: the lattice parameters read from shared
-// memory raise the register need; measured faster unbounded.)
+// Bounded to 128 registers (four 128-thread blocks per SM): the parameters
+// read from shared memory need more registers than the single-lattice
+// step's constant-bank operands; at 96 registers the kernel spills, and
+// unbounded (168 registers, three blocks) it ran 18 % slower.
 template <typename T, int BXT, int SCH>
-__global__ void __launch_bounds__(BXT)
+__global__ void __launch_bounds__(BXT, 512 / BXT)
 rc_batch_kernel(const BatchLattice<T>* __restrict__ lat, const int* __restrict__ active,
                 const int* __restrict__ begin, const int* __restrict__ counts, int parity) {
     extern __shared__ __align__(128) unsigned char smem[];

@@ -149,8 +149,8 @@ __device__ __forceinline__ void mbar_inval(unsigned bar) {
 // One block's work: segment `seg` of columns and row band `band` (of nbands)
 // of one lattice, from fin to fout.  smem: step_smem_bytes<T, BXT>() bytes.
 // Returns false when a wait ran out (the block must stop).
-// PT: KParams<T> (by value: a kernel parameter, read from the constant bank)
-// or const KParams<T>& (a lattice table in global memory).
+// PT: KParams<T> or const KParams<T>& (a kernel parameter, or the copy in
+// shared memory of a lattice of a batch).
 template <typename T, bool MASK, int BXT, typename I, int SCH, typename PT = KParams<T>>
 __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restrict__ fout,
                                            const PT p, int nbands, int seg, int band,
@@ -479,6 +479,9 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                 rho[j] = p.rho0 + d;
             }
             if (p.collide) {
+                // The collision takes its constants as a copy: bound to the
+                // parameter block by reference, the FP32 step spills a word
+                // and ran 1.5 % slower.
                 if constexpr (sizeof(T) == 4) {
                     // both cells in one float2 lane pair
                     static_assert(VC == 2, "FP32 collides its two cells as one float2");
@@ -488,8 +491,8 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                     const float2 D = make_float2(dp[0], dp[1]);
                     const float2 Gx = make_float2(dxr[0], dxr[1]), Gy = make_float2(dyr[0], dyr[1]);
                     const float2 R = (SCH == 1 || (SCH == 2 && p.raw))
-                                         ? collide_raw<float>(p.cc, F, D, Gx, Gy)
-                                         : collide<float>(p.cc, F, D, Gx, Gy);
+                                         ? collide_raw<float>(CollConst<float>(p.cc), F, D, Gx, Gy)
+                                         : collide<float>(CollConst<float>(p.cc), F, D, Gx, Gy);
                     rho[0] = R.x;
                     rho[1] = R.y;
 #pragma unroll
@@ -505,8 +508,8 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
 #pragma unroll
                         for (int i = 0; i < 9; ++i) F[i] = gcol[i][j];
                         rho[j] = (SCH == 1 || (SCH == 2 && p.raw))
-                                     ? collide_raw<T>(p.cc, F, dp[j], dxr[j], dyr[j])
-                                     : collide<T>(p.cc, F, dp[j], dxr[j], dyr[j]);
+                                     ? collide_raw<T>(CollConst<T>(p.cc), F, dp[j], dxr[j], dyr[j])
+                                     : collide<T>(CollConst<T>(p.cc), F, dp[j], dxr[j], dyr[j]);
 #pragma unroll
                         for (int i = 0; i < 9; ++i) gcol[i][j] = F[i];
                     }

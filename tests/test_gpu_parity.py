@@ -62,6 +62,25 @@ def test_parity(orc, name, precision):
     assert g.step_count == 20 and g.launch_count == 20
 
 
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+def test_fp32_setup_and_readout(orc, name):
+    """FP32 storage: the equilibrium set-up, evaluated as a deviation from
+    the rest state in FP32 arithmetic, against the oracle's FP64 equilibria;
+    and the FP32 read-out of rho and u against the oracle's FP64 moments of
+    the same stored state.  Both within a few FP32 roundings of the
+    deviations (|f - w rho0| <~ 0.05), far below what a dropped term moves."""
+    wl = CONFIGS[name]
+    o, g = oracle_of(orc, wl), gpu_of(wl, 32)
+    assert float(np.abs(g.get_f() - o.get_f()).max()) <= 1e-7
+    g.step(3)
+    o.set_f(g.get_f())
+    ro, uo, vo = o.moments()
+    rg, ug, vg = g.moments()
+    assert float(np.abs(rg - ro).max()) <= 1e-7
+    uscale = max(float(np.abs(uo).max()), float(np.abs(vo).max()))
+    assert float(max(np.abs(ug - uo).max(), np.abs(vg - vo).max())) <= 1e-6 * uscale + 1e-9
+
+
 @pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("name", sorted(CONFIGS))
 def test_parity_raw_moment_scheme(orc, name, precision):
