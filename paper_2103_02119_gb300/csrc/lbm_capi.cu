@@ -216,6 +216,14 @@ KParams<T> kparams_of(const lbm_params& q, const Geometry& g) {
     c.niah = L(-0.5 / a);
     c.iah2 = L(0.5 / a2);
     c.nia2 = L(-1.0 / a2);
+    c.qa = L(0.25 / a);
+    c.nqa = L(-0.25 / a);
+    c.qa2 = L(0.25 / a2);
+    c.lw3h = L(0.5 - 0.25 * w[3]);
+    c.lw4h = L(0.5 - 0.25 * w[4]);
+    c.nw3h = L(-0.5 * w[3]);
+    c.nw4h = L(-0.5 * w[4]);
+    k.forced = q.Fx != 0.0 || q.Fy != 0.0;
     k.lmask = g.lmask;
     k.collide = q.scheme >= 0;
     k.raw = q.scheme == 1;

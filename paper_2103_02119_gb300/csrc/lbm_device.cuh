@@ -48,6 +48,8 @@ struct CollConst {
     V lw3, lw4, lw5, lw6, lw7, lw8;    // 1 - w_j/2
     V nw3, nw4, nw5, nw6, nw7, nw8;    // -w_j
     V iah, niah, iah2, nia2;           // 1/(2a), -1/(2a), 1/(2a^2), -1/a^2
+    V qa, nqa, qa2;                    // halves of iah, niah, iah2
+    V lw3h, lw4h, nw3h, nw4h;          // halves of lw3, lw4, nw3, nw4
 };
 
 // Kernel parameters, converted once on the host to the arithmetic type T.
@@ -60,6 +62,7 @@ struct KParams {
     int moving;               // some wall moves
     int collide;              // 0: streaming and bounce-back only
     int raw;                  // 1: raw-moment collision (RNR-LBM, Sec. 3)
+    int forced;               // a body force is set
     T a, iah, iah2, cs2, rho0;  // a, 1/(2a), 1/(2a^2), c_s^2, rho0
     T wall_u[4][2];
     const uint8_t* __restrict__ lmask;  // per-cell link mask (nullable)
@@ -170,7 +173,7 @@ __device__ __forceinline__ float2 vrcp(float2 a) {
 // carried analytically so that FP32 only ever adds small numbers.
 //   f: deviations in, post-collision deviations out.  d = sum f (density
 //   deviation).  dxr, dyr: density gradient.  Returns rho.
-template <typename T>
+template <typename T, bool FORCE = true>
 __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
                                                        typename Lane<T>::V f[9],
                                                        typename Lane<T>::V d,
@@ -195,8 +198,8 @@ __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
     const V jx = vsub(k0[1], k0[2]);
     const V jy = vadd(vadd(ad[0], ad[1]), ad[2]);
     const V ir = vrcp(rho);
-    const V ux = vmul(vadd(jx, c.hFx), ir);
-    const V uy = vmul(vadd(jy, c.hFy), ir);
+    const V ux = FORCE ? vmul(vadd(jx, c.hFx), ir) : vmul(jx, ir);
+    const V uy = FORCE ? vmul(vadd(jy, c.hFy), ir) : vmul(jy, ir);
     const V nux = vneg(ux), nuy = vneg(uy);
 
     // Central moments along y of each column:
@@ -234,51 +237,59 @@ __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
 
     // Local strain rates, Eq. 37-38, from the raw non-equilibrium moments of
     // Eq. 34-35 (central ones minus the force terms u.F).
-    const V uFy = vmul(uy, c.Fy);
-    const V N3 = vsub(k3, vfma(ux, c.Fx, uFy));
-    const V N4 = vsub(k4, vsub(vmul(ux, c.Fx), uFy));
+    V N3 = k3, N4 = k4;
+    if constexpr (FORCE) {
+        const V uFy = vmul(uy, c.Fy);
+        N3 = vsub(k3, vfma(ux, c.Fx, uFy));
+        N4 = vsub(k4, vsub(vmul(ux, c.Fx), uFy));
+    }
     const V b1 = vfma(c.c15, ux2, c.b1c), b2 = vfma(c.c15, uy2, c.b2c);
     const V c1 = vfma(c.c15, ux2, c.c1c), c2 = vfma(c.nc15, uy2, c.c2c);
     const V gx = vmul(vmul(c.g1h, ux), dxr), gy = vmul(vmul(c.g2h, uy), dyr);
     const V R3 = vadd(vadd(N3, gx), gy);
     const V R4 = vsub(vadd(N4, gx), gy);
-    const V idet = vrcp(vmul(rho, vfma(b1, c2, vmul(vneg(b2), c1))));
-    const V dxux = vmul(vfma(c2, R3, vmul(vneg(b2), R4)), idet);
-    const V dyuy = vmul(vfma(b1, R4, vmul(vneg(c1), R3)), idet);
+    // the 2x2 solve gives rho d_x u_x and rho d_y u_y directly, which is all
+    // the corrections use
+    const V idet = vrcp(vfma(b1, c2, vmul(vneg(b2), c1)));
 
     // Corrections, Eq. 23-26: m3s + m3G = l3 (Px + Py), m4s + m4G = l4 (Px - Py).
-    const V rdx = vmul(rho, dxux), rdy = vmul(rho, dyuy);
+    const V rdx = vmul(vfma(c2, R3, vmul(vneg(b2), R4)), idet);
+    const V rdy = vmul(vfma(b1, R4, vmul(vneg(c1), R3)), idet);
     const V Px = vfma(c.g1i, vfma(ux, dxr, rdx), vmul(vmul(c.ng3, rdx), ux2));
     const V Py = vfma(c.g2i, vfma(uy, dyr, rdy), vmul(vmul(c.ng3, rdy), uy2));
 
     // Relaxation (Eq. 49 equilibria, Phi^c = (0, Fx, Fy, 0, ...)):
     // increments of the central moments.  kappa_1 = -Fx/2 before collision,
     // so its increment is Fx whatever omega_1 (same for y).
-    const V dk3 = vfma(c.lw3, vadd(Px, Py), vmul(c.nw3, k3));
-    const V dk4 = vfma(c.lw4, vsub(Px, Py), vmul(c.nw4, k4));
-    const V D20 = vmul(c.half, vadd(dk3, dk4)), D02 = vmul(c.half, vsub(dk3, dk4));
+    // (dk3, dk4 are the halves of the increments of k3, k4: halving the
+    // constants is exact, so D20 and D02 round as (dk3 +- dk4) / 2 would)
+    const V dk3 = vfma(c.lw3h, vadd(Px, Py), vmul(c.nw3h, k3));
+    const V dk4 = vfma(c.lw4h, vsub(Px, Py), vmul(c.nw4h, k4));
+    const V D20 = vadd(dk3, dk4), D02 = vsub(dk3, dk4);
     const V D11 = vmul(c.nw5, n11), D21 = vmul(c.nw6, n21), D12 = vmul(c.nw7, n12),
             D22 = vmul(c.nw8, n22);
 
     // Back along x: central -> raw x-moments -> the three columns (h[X][q],
     // X = 0, +1, -1), for q = 0: (0, Fx, D20), q = 1: (Fy, D11, D21),
-    // q = 2: (D02, D12, D22).
+    // q = 2: (D02, D12, D22).  The columns X = +-1 are kept doubled (their
+    // factor 1/2 goes into the constants of the expansion along y, exactly).
     V h[3][3];
     {
-        const V m2 = vfma(ux, c.twoFx, D20);  // m0 = 0, m1 = Fx
+        const V m2 = FORCE ? vfma(ux, c.twoFx, D20) : D20;  // m0 = 0, m1 = Fx
         h[0][0] = vneg(m2);
-        h[1][0] = vmul(c.half, vadd(m2, c.Fx));
-        h[2][0] = vmul(c.half, vsub(m2, c.Fx));
+        h[1][0] = FORCE ? vadd(m2, c.Fx) : m2;
+        h[2][0] = FORCE ? vsub(m2, c.Fx) : m2;
     }
     {
         const V m0[2] = {c.Fy, D02}, m1in[2] = {D11, D12}, m2in[2] = {D21, D22};
 #pragma unroll
         for (int q = 1; q < 3; ++q) {
-            const V m1 = vfma(ux, m0[q - 1], m1in[q - 1]);
+            const bool zero_m0 = q == 1 && !FORCE;  // m0 = Fy = 0
+            const V m1 = zero_m0 ? m1in[0] : vfma(ux, m0[q - 1], m1in[q - 1]);
             const V m2 = vfma(ux, vadd(m1in[q - 1], m1), m2in[q - 1]);
-            h[0][q] = vsub(m0[q - 1], m2);
-            h[1][q] = vmul(c.half, vadd(m2, m1));
-            h[2][q] = vmul(c.half, vsub(m2, m1));
+            h[0][q] = zero_m0 ? vneg(m2) : vsub(m0[q - 1], m2);
+            h[1][q] = vadd(m2, m1);
+            h[2][q] = vsub(m2, m1);
         }
     }
     // Back along y for each column, and add the increment.
@@ -289,9 +300,15 @@ __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
             const V m0 = h[X][0];
             const V m1 = vfma(uy, m0, h[X][1]);
             const V m2 = vfma(uy, vadd(h[X][1], m1), h[X][2]);
-            f[iz[X]] = vadd(f[iz[X]], vfma(c.nia2, m2, m0));
-            f[ip[X]] = vfma(c.iah2, m2, vfma(c.iah, m1, f[ip[X]]));
-            f[im[X]] = vfma(c.iah2, m2, vfma(c.niah, m1, f[im[X]]));
+            if (X == 0) {
+                f[0] = vadd(f[0], vfma(c.nia2, m2, m0));
+                f[2] = vfma(c.iah2, m2, vfma(c.iah, m1, f[2]));
+                f[4] = vfma(c.iah2, m2, vfma(c.niah, m1, f[4]));
+            } else {
+                f[iz[X]] = vfma(c.half, vfma(c.nia2, m2, m0), f[iz[X]]);
+                f[ip[X]] = vfma(c.qa2, m2, vfma(c.qa, m1, f[ip[X]]));
+                f[im[X]] = vfma(c.qa2, m2, vfma(c.nqa, m1, f[im[X]]));
+            }
         }
     }
     return rho;

@@ -10,9 +10,10 @@
 // time.
 //
 // The scheme is a template parameter of the block's work (SCH: 0 RC-LBM,
-// 1 RNR-LBM, 2 chosen per lattice at run time), so that a single-lattice
-// kernel carries only its own collision; scheme -1 (no collision) is a run
-// time switch of every kernel.
+// 1 RNR-LBM, 2 chosen per lattice at run time, 3 RC-LBM without a body
+// force, its force terms compiled out), so that a single-lattice kernel
+// carries only its own collision; scheme -1 (no collision) is a run time
+// switch of every kernel.
 //
 // Staging.  The populations a row pulls (plane i of the source row
 // y - e_iy, columns x0-4 .. x0+W+3) are brought into shared memory by TMA
@@ -492,7 +493,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                     const float2 Gx = make_float2(dxr[0], dxr[1]), Gy = make_float2(dyr[0], dyr[1]);
                     const float2 R = (SCH == 1 || (SCH == 2 && p.raw))
                                          ? collide_raw<float>(CollConst<float>(p.cc), F, D, Gx, Gy)
-                                         : collide<float>(CollConst<float>(p.cc), F, D, Gx, Gy);
+                                         : collide<float, SCH != 3>(CollConst<float>(p.cc), F, D, Gx, Gy);
                     rho[0] = R.x;
                     rho[1] = R.y;
 #pragma unroll
@@ -509,7 +510,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                         for (int i = 0; i < 9; ++i) F[i] = gcol[i][j];
                         rho[j] = (SCH == 1 || (SCH == 2 && p.raw))
                                      ? collide_raw<T>(CollConst<T>(p.cc), F, dp[j], dxr[j], dyr[j])
-                                     : collide<T>(CollConst<T>(p.cc), F, dp[j], dxr[j], dyr[j]);
+                                     : collide<T, SCH != 3>(CollConst<T>(p.cc), F, dp[j], dxr[j], dyr[j]);
 #pragma unroll
                         for (int i = 0; i < 9; ++i) gcol[i][j] = F[i];
                     }
