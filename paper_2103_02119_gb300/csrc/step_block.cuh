@@ -496,10 +496,15 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                                          : collide<float, SCH != 3>(CollConst<float>(p.cc), F, D, Gx, Gy);
                     rho[0] = R.x;
                     rho[1] = R.y;
+                    // A solid cell keeps its zeros.  Without a mask the only
+                    // such cells are the inactive columns past nx, stored
+                    // into the row padding, which nothing reads (no fluid
+                    // cell pulls from it, no read-out visits it): they take
+                    // the collision's result unselected.
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        if (sbp[0] != 0xFFu) gcol[i][0] = F[i].x;
-                        if (sbp[1] != 0xFFu) gcol[i][1] = F[i].y;
+                        if (!MASK || sbp[0] != 0xFFu) gcol[i][0] = F[i].x;
+                        if (!MASK || sbp[1] != 0xFFu) gcol[i][1] = F[i].y;
                     }
                 } else {
 #pragma unroll
