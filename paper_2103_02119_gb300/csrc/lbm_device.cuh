@@ -173,6 +173,13 @@ __device__ __forceinline__ float2 vrcp(float2 a) {
 // carried analytically so that FP32 only ever adds small numbers.
 //   f: deviations in, post-collision deviations out.  d = sum f (density
 //   deviation).  dxr, dyr: density gradient.  Returns rho.
+// A constant of the collision as an operand of both lanes: the stored pair
+// holds the same value twice, and the collision reads its low half for both
+// (which needs fewer registers than the pair itself: the FP32 step then
+// spills nothing and ran 1.4 % faster, the batch 2 %).
+__device__ __forceinline__ float2 bc(float2 v) { return make_float2(v.x, v.x); }
+__device__ __forceinline__ double bc(double v) { return v; }
+
 template <typename T, bool FORCE = true>
 __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
                                                        typename Lane<T>::V f[9],
@@ -190,16 +197,16 @@ __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             sq[q] = vadd(gp[q], gm[q]);
-            ad[q] = vmul(c.a, vsub(gp[q], gm[q]));
+            ad[q] = vmul(bc(c.a), vsub(gp[q], gm[q]));
             k0[q] = vadd(gz[q], sq[q]);
         }
     }
-    const V rho = vadd(c.rho0, d);
+    const V rho = vadd(bc(c.rho0), d);
     const V jx = vsub(k0[1], k0[2]);
     const V jy = vadd(vadd(ad[0], ad[1]), ad[2]);
     const V ir = vrcp(rho);
-    const V ux = FORCE ? vmul(vadd(jx, c.hFx), ir) : vmul(jx, ir);
-    const V uy = FORCE ? vmul(vadd(jy, c.hFy), ir) : vmul(jy, ir);
+    const V ux = FORCE ? vmul(vadd(jx, bc(c.hFx)), ir) : vmul(jx, ir);
+    const V uy = FORCE ? vmul(vadd(jy, bc(c.hFy)), ir) : vmul(jy, ir);
     const V nux = vneg(ux), nuy = vneg(uy);
 
     // Central moments along y of each column:
@@ -207,7 +214,7 @@ __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         k1[q] = vfma(nuy, k0[q], ad[q]);
-        k2[q] = vfma(nuy, vadd(ad[q], k1[q]), vmul(c.a2, sq[q]));
+        k2[q] = vfma(nuy, vadd(ad[q], k1[q]), vmul(bc(c.a2), sq[q]));
     }
     // Along x: C[p][q] = sum_X (e_x - u_x)^p k_q(X).
     V C[3][3];
@@ -226,26 +233,26 @@ __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
     // moments of rho0 w about u.
     const V ux2 = vmul(ux, ux), uy2 = vmul(uy, uy);
     const V nd = vneg(d);
-    const V n20 = vfma(c.rho0, ux2, vfma(nd, c.cs2, C[2][0]));
-    const V n02 = vfma(c.rho0, uy2, vfma(nd, c.cs2, C[0][2]));
-    const V n11 = vfma(vmul(c.rho0, ux), uy, C[1][1]);
-    const V n21 = vfma(vmul(c.nrho0, uy), vadd(c.cs2, ux2), C[2][1]);
-    const V n12 = vfma(vmul(c.nrho0, ux), vadd(c.cs2, uy2), C[1][2]);
-    const V n22 = vfma(c.rho0, vfma(c.cs2, vadd(ux2, uy2), vmul(ux2, uy2)),
-                       vfma(nd, c.cs4, C[2][2]));
+    const V n20 = vfma(bc(c.rho0), ux2, vfma(nd, bc(c.cs2), C[2][0]));
+    const V n02 = vfma(bc(c.rho0), uy2, vfma(nd, bc(c.cs2), C[0][2]));
+    const V n11 = vfma(vmul(bc(c.rho0), ux), uy, C[1][1]);
+    const V n21 = vfma(vmul(bc(c.nrho0), uy), vadd(bc(c.cs2), ux2), C[2][1]);
+    const V n12 = vfma(vmul(bc(c.nrho0), ux), vadd(bc(c.cs2), uy2), C[1][2]);
+    const V n22 = vfma(bc(c.rho0), vfma(bc(c.cs2), vadd(ux2, uy2), vmul(ux2, uy2)),
+                       vfma(nd, bc(c.cs4), C[2][2]));
     const V k3 = vadd(n20, n02), k4 = vsub(n20, n02);
 
     // Local strain rates, Eq. 37-38, from the raw non-equilibrium moments of
     // Eq. 34-35 (central ones minus the force terms u.F).
     V N3 = k3, N4 = k4;
     if constexpr (FORCE) {
-        const V uFy = vmul(uy, c.Fy);
-        N3 = vsub(k3, vfma(ux, c.Fx, uFy));
-        N4 = vsub(k4, vsub(vmul(ux, c.Fx), uFy));
+        const V uFy = vmul(uy, bc(c.Fy));
+        N3 = vsub(k3, vfma(ux, bc(c.Fx), uFy));
+        N4 = vsub(k4, vsub(vmul(ux, bc(c.Fx)), uFy));
     }
-    const V b1 = vfma(c.c15, ux2, c.b1c), b2 = vfma(c.c15, uy2, c.b2c);
-    const V c1 = vfma(c.c15, ux2, c.c1c), c2 = vfma(c.nc15, uy2, c.c2c);
-    const V gx = vmul(vmul(c.g1h, ux), dxr), gy = vmul(vmul(c.g2h, uy), dyr);
+    const V b1 = vfma(bc(c.c15), ux2, bc(c.b1c)), b2 = vfma(bc(c.c15), uy2, bc(c.b2c));
+    const V c1 = vfma(bc(c.c15), ux2, bc(c.c1c)), c2 = vfma(bc(c.nc15), uy2, bc(c.c2c));
+    const V gx = vmul(vmul(bc(c.g1h), ux), dxr), gy = vmul(vmul(bc(c.g2h), uy), dyr);
     const V R3 = vadd(vadd(N3, gx), gy);
     const V R4 = vsub(vadd(N4, gx), gy);
     // the 2x2 solve gives rho d_x u_x and rho d_y u_y directly, which is all
@@ -255,19 +262,19 @@ __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
     // Corrections, Eq. 23-26: m3s + m3G = l3 (Px + Py), m4s + m4G = l4 (Px - Py).
     const V rdx = vmul(vfma(c2, R3, vmul(vneg(b2), R4)), idet);
     const V rdy = vmul(vfma(b1, R4, vmul(vneg(c1), R3)), idet);
-    const V Px = vfma(c.g1i, vfma(ux, dxr, rdx), vmul(vmul(c.ng3, rdx), ux2));
-    const V Py = vfma(c.g2i, vfma(uy, dyr, rdy), vmul(vmul(c.ng3, rdy), uy2));
+    const V Px = vfma(bc(c.g1i), vfma(ux, dxr, rdx), vmul(vmul(bc(c.ng3), rdx), ux2));
+    const V Py = vfma(bc(c.g2i), vfma(uy, dyr, rdy), vmul(vmul(bc(c.ng3), rdy), uy2));
 
     // Relaxation (Eq. 49 equilibria, Phi^c = (0, Fx, Fy, 0, ...)):
     // increments of the central moments.  kappa_1 = -Fx/2 before collision,
     // so its increment is Fx whatever omega_1 (same for y).
     // (dk3, dk4 are the halves of the increments of k3, k4: halving the
     // constants is exact, so D20 and D02 round as (dk3 +- dk4) / 2 would)
-    const V dk3 = vfma(c.lw3h, vadd(Px, Py), vmul(c.nw3h, k3));
-    const V dk4 = vfma(c.lw4h, vsub(Px, Py), vmul(c.nw4h, k4));
+    const V dk3 = vfma(bc(c.lw3h), vadd(Px, Py), vmul(bc(c.nw3h), k3));
+    const V dk4 = vfma(bc(c.lw4h), vsub(Px, Py), vmul(bc(c.nw4h), k4));
     const V D20 = vadd(dk3, dk4), D02 = vsub(dk3, dk4);
-    const V D11 = vmul(c.nw5, n11), D21 = vmul(c.nw6, n21), D12 = vmul(c.nw7, n12),
-            D22 = vmul(c.nw8, n22);
+    const V D11 = vmul(bc(c.nw5), n11), D21 = vmul(bc(c.nw6), n21), D12 = vmul(bc(c.nw7), n12),
+            D22 = vmul(bc(c.nw8), n22);
 
     // Back along x: central -> raw x-moments -> the three columns (h[X][q],
     // X = 0, +1, -1), for q = 0: (0, Fx, D20), q = 1: (Fy, D11, D21),
@@ -275,13 +282,13 @@ __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
     // factor 1/2 goes into the constants of the expansion along y, exactly).
     V h[3][3];
     {
-        const V m2 = FORCE ? vfma(ux, c.twoFx, D20) : D20;  // m0 = 0, m1 = Fx
+        const V m2 = FORCE ? vfma(ux, bc(c.twoFx), D20) : D20;  // m0 = 0, m1 = Fx
         h[0][0] = vneg(m2);
-        h[1][0] = FORCE ? vadd(m2, c.Fx) : m2;
-        h[2][0] = FORCE ? vsub(m2, c.Fx) : m2;
+        h[1][0] = FORCE ? vadd(m2, bc(c.Fx)) : m2;
+        h[2][0] = FORCE ? vsub(m2, bc(c.Fx)) : m2;
     }
     {
-        const V m0[2] = {c.Fy, D02}, m1in[2] = {D11, D12}, m2in[2] = {D21, D22};
+        const V m0[2] = {bc(c.Fy), D02}, m1in[2] = {D11, D12}, m2in[2] = {D21, D22};
 #pragma unroll
         for (int q = 1; q < 3; ++q) {
             const bool zero_m0 = q == 1 && !FORCE;  // m0 = Fy = 0
@@ -301,13 +308,13 @@ __device__ __forceinline__ typename Lane<T>::V collide(const CollConst<T>& c,
             const V m1 = vfma(uy, m0, h[X][1]);
             const V m2 = vfma(uy, vadd(h[X][1], m1), h[X][2]);
             if (X == 0) {
-                f[0] = vadd(f[0], vfma(c.nia2, m2, m0));
-                f[2] = vfma(c.iah2, m2, vfma(c.iah, m1, f[2]));
-                f[4] = vfma(c.iah2, m2, vfma(c.niah, m1, f[4]));
+                f[0] = vadd(f[0], vfma(bc(c.nia2), m2, m0));
+                f[2] = vfma(bc(c.iah2), m2, vfma(bc(c.iah), m1, f[2]));
+                f[4] = vfma(bc(c.iah2), m2, vfma(bc(c.niah), m1, f[4]));
             } else {
-                f[iz[X]] = vfma(c.half, vfma(c.nia2, m2, m0), f[iz[X]]);
-                f[ip[X]] = vfma(c.qa2, m2, vfma(c.qa, m1, f[ip[X]]));
-                f[im[X]] = vfma(c.qa2, m2, vfma(c.nqa, m1, f[im[X]]));
+                f[iz[X]] = vfma(bc(c.half), vfma(bc(c.nia2), m2, m0), f[iz[X]]);
+                f[ip[X]] = vfma(bc(c.qa2), m2, vfma(bc(c.qa), m1, f[ip[X]]));
+                f[im[X]] = vfma(bc(c.qa2), m2, vfma(bc(c.nqa), m1, f[im[X]]));
             }
         }
     }
