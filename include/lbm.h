@@ -299,10 +299,10 @@ lbm_status lbm_batch_set_shape(lbm_batch* b, int block_x, int rows_per_band);
 lbm_status lbm_batch_get_shape(const lbm_batch* b, int* block_x, int* rows_per_band);
 
 /* Autotuner: times trial_steps (>= 1) steps of the active lattices at each
- * block_x in {32, 64, 128} and rows_per_band in {8, 16, 32, 64} (one warm-up
+ * block_x in {32, 64, 128} and rows_per_band in {1, 2, 4, 8, 16, 32, 64} (one warm-up
  * step each, CUDA events on the batch's stream), keeps the fastest shape and
  * returns it (outputs nullable).  The trial steps are real steps of the
- * active lattices (12 (trial_steps + 1) in all): the shape does not change
+ * active lattices (21 (trial_steps + 1) in all): the shape does not change
  * the results.  Synchronous. */
 lbm_status lbm_batch_tune(lbm_batch* b, int trial_steps, int* block_x,
                           int* rows_per_band);
