@@ -258,38 +258,48 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         return any;
     };
 
-    // the issuing warp: copies of the source rows of iteration k into its stage; lane 0
-    // announces the byte count on the stage's mbarrier, lanes 0..8 copy one
-    // plane each, lane 9 the row of the link mask (columns x0 .. x0 + mbytes;
-    // x0 and the row pitch are multiples of 32, so the copy is 16-byte
-    // aligned and stays inside the mask)
+    // the issuing warp's lane 0: copies of the source rows of iteration k
+    // into its stage, one per plane, and the row of the link mask (columns
+    // x0 .. x0 + mbytes; x0 and the row pitch are multiples of 32, so the
+    // copy is 16-byte aligned and stays inside the mask).  One lane issues
+    // them all: every operand is then the same across the warp, so the
+    // copies need no serialisation over lanes.
     const unsigned mbytes = (unsigned)min(W, p.pitch - x0);
     const unsigned sm0 = smem_u32(smask);
     auto issue = [&](int k) {
+        if (lane != 0) return;
         const int s = k % kStages;
         const unsigned bar = bar0 + 8u * s;
         const int r = rfirst + dir * k;
         const bool ok = row_valid(r);
         const int rr = ok ? wrap_row(r) : 0;
-        unsigned bytes = 0;
-        int sr_mine = -1;
+        // source row of the planes with e_y = 0, +1, -1
+        int srow[3];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
+        for (int e = 0; e < 3; ++e) {
             int sr = -1;
             if (ok) {
-                sr = rr - ey(i);
+                sr = rr - (e == 0 ? 0 : (e == 1 ? 1 : -1));
                 if (sr < 0 || sr >= p.ny) sr = p.py ? wrap_row(sr) : -1;
             }
+            srow[e] = sr;
+        }
+        unsigned bytes = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sr = srow[ey(i) == 0 ? 0 : (ey(i) > 0 ? 1 : 2)];
             if (sr >= 0) bytes += cbytes;
-            if (i == lane) sr_mine = sr;
         }
         if (MASK && ok) bytes += mbytes;
-        if (lane == 0) mbar_expect_tx(bar, bytes);
-        __syncwarp();
-        if (lane < 9 && sr_mine >= 0)
-            bulk_g2s(st0 + (unsigned)(((s * 9 + lane) * SW + dshift) * sizeof(T)),
-                     fin + (lane * pl + (I)sr_mine * rs + wstart), cbytes, bar);
-        if (MASK && lane == 9 && ok)
+        mbar_expect_tx(bar, bytes);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sr = srow[ey(i) == 0 ? 0 : (ey(i) > 0 ? 1 : 2)];
+            if (sr >= 0)
+                bulk_g2s(st0 + (unsigned)(((s * 9 + i) * SW + dshift) * sizeof(T)),
+                         fin + (i * pl + (I)sr * rs + wstart), cbytes, bar);
+        }
+        if (MASK && ok)
             bulk_g2s(sm0 + (unsigned)(s * W), p.lmask + ((I)rr * pitch + x0), mbytes, bar);
     };
 
