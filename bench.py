@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the repo's own copy-bandwidth and FP64-FMA measurements")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true",
@@ -169,9 +171,9 @@ def step_kernel_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(precision, cells):
-    """DRAM bytes per launch from the committed ncu summary, scaled to this
-    grid, or None when the kernel has changed since it was captured."""
+def profiled(precision, key):
+    """A per-cell figure of the committed ncu summary of the step kernel, or
+    None when the kernel has changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "rc_step_traffic.json")
     try:
         with open(path) as fh:
@@ -181,7 +183,26 @@ def profiled_traffic(precision, cells):
     e = d.get(f"fp{precision}")
     if not e or e.get("kernel_sha") != step_kernel_hash():
         return None
-    return e["dram_bytes_per_cell"] * cells
+    return e.get(key)
+
+
+def profiled_traffic(precision, cells):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this
+    grid, or None when the kernel has changed since it was captured."""
+    b = profiled(precision, "dram_bytes_per_cell")
+    return None if b is None else b * cells
+
+
+def repo_peaks(stream):
+    """The roofs measured by the library's own kernels: device-to-device copy
+    of 2 GiB buffers (well above the L2) and the FP64 FMA rate."""
+    from paper_2103_02119_gb300 import lbm
+    copy = lbm.lbm_peak_copy_gbs(2 << 30, 20, stream)
+    dfma = lbm.lbm_peak_fp64_gflops(20000, stream)
+    return {"copy_gbs": copy, "fp64_gflops": dfma,
+            "note": "library kernels: 16-byte-word grid-stride copy between two 2 GiB "
+                    "buffers (GB/s = read + write); 8 independent DFMA chains per thread "
+                    "(an FMA counts two flops)"}
 
 
 # ------------------------------------------------------- multi-rank timing --
@@ -502,6 +523,10 @@ def main():
                 "peak_kind": peak_kind, "kernel": f"rc_step_kernel<fp{args.precision}>",
                 "algorithmic_bytes_per_cell": BYTES_PER_CELL[args.precision]}
     e2e_res = None if args.no_e2e else e2e(lat, wl, torch, args.e2e_chunk, args.e2e_steps)
+    peaks = None
+    if rank == 0 and not args.no_peaks:
+        peaks = repo_peaks(stream)
+        roofline["frac_vs_repo_copy"] = achieved / peaks["copy_gbs"]
 
     fp64 = None
     if not args.no_fp64 and args.precision == 32:
@@ -513,6 +538,14 @@ def main():
         fp64 = {"value": cells * n64 / s64 / 1e6, "unit": "MLUPS", "steps": n64,
                 "roofline": {"bound": "alu", "hbm_achieved": a64, "hbm_peak": peak,
                              "unit": "GB/s", "hbm_frac": a64 / peak}}
+        # the FP64 roof: FP64 flops per cell counted by ncu (DFMA twice,
+        # DADD, DMUL) over the repo's FMA-rate measurement
+        fl = profiled(64, "fp64_flops_per_cell")
+        if fl is not None and peaks is not None:
+            alu = fp64["value"] * 1e6 * fl / 1e9
+            fp64["roofline"].update({"fp64_flops_per_cell": fl, "alu_achieved": alu,
+                                     "alu_peak": peaks["fp64_gflops"], "alu_unit": "GFLOP/s",
+                                     "alu_frac": alu / peaks["fp64_gflops"]})
         lat64.close()
     else:
         lat.close()
@@ -544,7 +577,7 @@ def main():
             "config": workload_config(args, wl), "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches,
             "clocks": clk.summary(), "fp64": fp64, "batch": batch, "small_lattice": small,
-            "warm_start": warm,
+            "warm_start": warm, "repo_peaks": peaks,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

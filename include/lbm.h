@@ -326,6 +326,26 @@ int64_t lbm_batch_launch_count(const lbm_batch* b);
  * when b is NULL); never NULL. */
 const char* lbm_batch_last_error(const lbm_batch* b);
 
+/* ---- Measurement: the roofs the step is reported against ----
+ * Neither has a counterpart in the paper; they measure the GPU, not the
+ * method.  Both run on the current device, are synchronous, allocate and
+ * free their own device buffers, and return LBM_ERR_INVALID for a bad
+ * argument (nothing is run), LBM_ERR_OOM or LBM_ERR_CUDA otherwise.
+ *
+ * Device-to-device copy bandwidth (the HBM roof of FP32 storage, whose step
+ * reads and writes each population once): allocates two buffers of `bytes`
+ * (a multiple of 16, >= 16), copies one into the other once untimed and
+ * `iters` (>= 1) times timed with CUDA events on `stream` (nullable: the
+ * default stream), in 16-byte words by 8 blocks of 256 threads per SM;
+ * *gbs = 2 bytes iters / time / 1e9 (read plus write). */
+lbm_status lbm_peak_copy_gbs(size_t bytes, int iters, void* stream, double* gbs);
+
+/* FP64 fused multiply-add rate (the roof of FP64 storage, whose step is
+ * bound by the FP64 pipe): 4 blocks of 256 threads per SM, each thread
+ * running 8 independent chains of `iters` (>= 1) FMAs, one untimed and one
+ * timed launch on `stream`; *gflops = 2 FMAs / time / 1e9. */
+lbm_status lbm_peak_fp64_gflops(int iters, void* stream, double* gflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -134,6 +134,8 @@ def _load():
     L.lbm_nn_launch_count.restype = ctypes.c_int64
     L.lbm_nn_last_error.argtypes = [_P]
     L.lbm_nn_last_error.restype = ctypes.c_char_p
+    L.lbm_peak_copy_gbs.argtypes = [ctypes.c_size_t, ctypes.c_int, _P, _D]
+    L.lbm_peak_fp64_gflops.argtypes = [ctypes.c_int, _P, _D]
     return L
 
 
@@ -745,3 +747,23 @@ class Lattice:
     @property
     def launch_count(self) -> int:
         return lbm_launch_count(self.h)
+
+
+# ------------------------------------------------------------ measurement --
+
+def lbm_peak_copy_gbs(nbytes, iters, stream=None) -> float:
+    """Device-to-device copy bandwidth in GB/s (read plus write)."""
+    out = ctypes.c_double()
+    st = lib.lbm_peak_copy_gbs(int(nbytes), int(iters), _stream_ptr(stream), ctypes.byref(out))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_peak_copy_gbs failed")
+    return out.value
+
+
+def lbm_peak_fp64_gflops(iters, stream=None) -> float:
+    """FP64 fused multiply-add rate in GFLOP/s (an FMA counts two)."""
+    out = ctypes.c_double()
+    st = lib.lbm_peak_fp64_gflops(int(iters), _stream_ptr(stream), ctypes.byref(out))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_peak_fp64_gflops failed")
+    return out.value

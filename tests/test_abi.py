@@ -157,3 +157,13 @@ def test_nn_invalid_shapes_rejected_on_host(L):
     assert L.lib.lbm_nn_param_count(None) == 0
     assert L.lib.lbm_nn_forward(None, None, 1, None) == L.LBM_ERR_INVALID
     L.lib.lbm_nn_destroy(None)
+
+
+def test_peak_probes_reject_bad_arguments_on_host(L):
+    out = ctypes.c_double(-1.0)
+    for nbytes, iters in [(0, 1), (8, 1), (1000, 1), (1 << 20, 0)]:
+        assert L.lib.lbm_peak_copy_gbs(nbytes, iters, None, ctypes.byref(out)) == L.LBM_ERR_INVALID
+    assert L.lib.lbm_peak_copy_gbs(1 << 20, 1, None, None) == L.LBM_ERR_INVALID
+    assert L.lib.lbm_peak_fp64_gflops(0, None, ctypes.byref(out)) == L.LBM_ERR_INVALID
+    assert L.lib.lbm_peak_fp64_gflops(10, None, None) == L.LBM_ERR_INVALID
+    assert out.value == -1.0
