@@ -18,7 +18,7 @@
 // Staging.  The populations a row pulls (plane i of the source row
 // y - e_iy, columns x0-4 .. x0+W+3) are brought into shared memory by TMA
 // bulk copies (cp.async.bulk, completion counted on an mbarrier), issued by
-// lanes of one warp two rows ahead into a two-stage ring.  A thread reads its
+// one lane three rows ahead into a three-stage ring.  A thread reads its
 // cells' nine populations with vector shared loads (plus one scalar load for
 // the planes shifted along x) and keeps them in registers until the row
 // collides one iteration later, so a stage is free as soon as its row is read.  Cells next to a wall or a solid, and the
@@ -31,7 +31,7 @@
 //      in shared memory (lanes of warp 0 add the density of the two columns
 //      just outside the segment, one population per lane);
 //   2. one barrier (which also votes on a timed-out wait);
-//   3. the issuing warp refills the stage of row k with row k+2;
+//   3. the issuing lane refills the stage of row k with row k+3;
 //   4. row k-1 collides from the populations kept in registers: its density
 //      gradient comes from the ring by central differences (spacing 2 along
 //      x, 2a along y; a wall or solid neighbour mirrors the cell's own
@@ -51,7 +51,7 @@ namespace lbm {
 
 namespace {
 
-constexpr int kStages = 2;              // stage ring depth (copies run 2 rows ahead)
+constexpr int kStages = 3;              // stage ring depth (copies run 3 rows ahead)
 constexpr int kHalo = 4;                // staged columns on each side of a segment
 constexpr unsigned kSpinLimit = 1u << 22;
 
