@@ -538,14 +538,21 @@ def main():
         fp64 = {"value": cells * n64 / s64 / 1e6, "unit": "MLUPS", "steps": n64,
                 "roofline": {"bound": "alu", "hbm_achieved": a64, "hbm_peak": peak,
                              "unit": "GB/s", "hbm_frac": a64 / peak}}
-        # the FP64 roof: FP64 flops per cell counted by ncu (DFMA twice,
-        # DADD, DMUL) over the repo's FMA-rate measurement
+        # the FP64 roof: FP64 instructions per cell counted by ncu (DFMA,
+        # DADD, DMUL each take the pipe once) against the FMA rate the
+        # library measures (one FMA = two flops); the flop count (DFMA
+        # twice) is reported beside it
+        ops = profiled(64, "fp64_pipe_ops_per_cell")
         fl = profiled(64, "fp64_flops_per_cell")
-        if fl is not None and peaks is not None:
-            alu = fp64["value"] * 1e6 * fl / 1e9
-            fp64["roofline"].update({"fp64_flops_per_cell": fl, "alu_achieved": alu,
-                                     "alu_peak": peaks["fp64_gflops"], "alu_unit": "GFLOP/s",
-                                     "alu_frac": alu / peaks["fp64_gflops"]})
+        if ops is not None and fl is not None and peaks is not None:
+            rate = fp64["value"] * 1e6
+            pk = peaks["fp64_gflops"]
+            fp64["roofline"].update({
+                "fp64_pipe_ops_per_cell": ops, "fp64_flops_per_cell": fl,
+                "alu_achieved": rate * ops / 1e9, "alu_peak": pk / 2, "alu_unit": "Gop/s",
+                "alu_frac": rate * ops / 1e9 / (pk / 2),
+                "alu_flops_achieved": rate * fl / 1e9, "alu_flops_peak": pk,
+                "alu_flops_frac": rate * fl / 1e9 / pk})
         lat64.close()
     else:
         lat.close()
