@@ -165,7 +165,8 @@ def measured_peaks():
 
 def step_kernel_hash():
     h = hashlib.sha256()
-    for f in ("rc_step.cu", "rnr_step.cu", "step_block.cuh", "lbm_device.cuh"):
+    for f in ("rc_step.cu", "rc_free_step.cu", "rnr_step.cu", "step_block.cuh",
+              "lbm_device.cuh"):
         with open(os.path.join(ROOT, "paper_2103_02119_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -25,6 +25,11 @@ cudaError_t launch_step(const T* fin, T* fout, const KParams<T>& p, int bx, int 
 template <typename T>
 cudaError_t launch_step_rnr(const T* fin, T* fout, const KParams<T>& p, int bx, int nbands,
                             cudaStream_t s);
+// The RC-LBM step of a lattice without a body force (the force terms of the
+// collision compiled out).
+template <typename T>
+cudaError_t launch_step_free(const T* fin, T* fout, const KParams<T>& p, int bx, int nbands,
+                             cudaStream_t s);
 template <typename T>
 int step_occupancy(int bx, bool mask);
 // columns of lattice one block of bx threads of the step kernel covers

@@ -110,10 +110,9 @@ template <typename T>
 cudaError_t launch_step(const T* fin, T* fout, const KParams<T>& p, int bx, int nbands,
                         cudaStream_t s) {
     if (p.collide && p.raw) return launch_step_rnr<T>(fin, fout, p, bx, nbands, s);
-    // FP32 flows without a body force take the collision with the force
-    // terms compiled out
-    if constexpr (sizeof(T) == 4)
-        if (p.collide && !p.forced) return launch_step_scheme<T, 3>(fin, fout, p, bx, nbands, s);
+    // flows without a body force take the collision with the force terms
+    // compiled out
+    if (p.collide && !p.forced) return launch_step_free<T>(fin, fout, p, bx, nbands, s);
     return launch_step_scheme<T, 0>(fin, fout, p, bx, nbands, s);
 }
 template cudaError_t launch_step<float>(const float*, float*, const KParams<float>&,
