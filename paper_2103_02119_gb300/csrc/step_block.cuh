@@ -345,15 +345,20 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                 } else if (MASK && !(p.px && (cx == 0 || cx == p.nx - 1))) {
                     // With a mask (walls and solids anywhere): an open link's
                     // source is staged; a blocked one bounces back the cell's
-                    // own opposite population, the only global read.  (Without
-                    // one, only the edge rows and columns come here, and the
-                    // full gather measured faster.)
+                    // own opposite population, a global read unless the link
+                    // is horizontal.  (Without a mask only the edge rows and
+                    // columns come here, and the full gather measured faster.)
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        if (i > 0 && ((sb[j] >> (i - 1)) & 1u))
-                            f[i] = __ldg(fin + (opp(i) * pl + (I)rr * rs + cx));
-                        else
+                        if (i > 0 && ((sb[j] >> (i - 1)) & 1u)) {
+                            // plane opp(i) is staged at this row when e_iy = 0
+                            if (ey(i) == 0)
+                                f[i] = b[opp(i) * SW + j];
+                            else
+                                f[i] = __ldg(fin + (opp(i) * pl + (I)rr * rs + cx));
+                        } else {
                             f[i] = b[i * SW + j - ex(i)];
+                        }
                     }
                 } else {
                     pull(fin, p, cx, rr, sb[j], f);
