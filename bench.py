@@ -432,14 +432,15 @@ def warm_start_measure(torch, ntrain, epochs, n=32, ntest=32):
 
 # -------------------------------------------------------------- oracle arm --
 
-def oracle_mlups(wl, rows, seconds, warmup_steps=0, steps=None):
-    """The FP64 oracle as it stands, all host cores, on the same cavity with
-    `rows` rows; returns (MLUPS, threads, steps, sample description)."""
+def oracle_mlups(wl, rows, seconds, warmup_steps=0, steps=None, nthreads=0):
+    """The FP64 oracle as it stands, on all host cores (nthreads = 0) or the
+    given number of threads, on the same cavity with `rows` rows; returns
+    (MLUPS, threads, steps, sample description)."""
     import oracle
     sub = wl.with_(ny=rows)
     p = oracle.OracleParams.make(sub.nx, sub.ny, sub.a, sub.cs2, sub.omega,
                                  periodic_x=sub.periodic_x, periodic_y=sub.periodic_y,
-                                 wall_u=sub.wall_u)
+                                 wall_u=sub.wall_u, nthreads=nthreads)
     o = oracle.Oracle(p)
     if warmup_steps:
         o.step(warmup_steps)
@@ -575,6 +576,9 @@ def main():
         mlups, threads, steps, desc, _ = oracle_mlups(wl, wl.ny, args.cpu_seconds)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                "sample": desc}
+        # the same oracle on one thread, on a smaller slab of the cavity
+        m1, _, _, d1, _ = oracle_mlups(wl, 256, min(5.0, args.cpu_seconds), nthreads=1)
+        cpu["single_thread"] = {"value": m1, "unit": "MLUPS", "cores": 1, "sample": d1}
 
     if rank == 0:
         line = {
