@@ -164,11 +164,17 @@ def measured_peaks():
 
 
 def step_kernel_hash():
+    """Hash of the step kernels' code (comments and whitespace left out, so
+    that only a change of the code itself invalidates recorded counters)."""
+    import re
     h = hashlib.sha256()
     for f in ("rc_step.cu", "rc_free_step.cu", "rnr_step.cu", "step_block.cuh",
               "lbm_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2103_02119_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2103_02119_gb300", "csrc", f)) as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

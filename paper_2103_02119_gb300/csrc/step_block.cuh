@@ -1,7 +1,8 @@
 // step_block.cuh -- the fused collide-and-stream step of the RC-LBM
 // (arXiv 2103.02119, Sec. 4) and of its raw-moment variant (RNR-LBM, Sec. 3)
 // for sm_103a, FP32 and FP64: one thread block's work.  Included by the
-// translation units that instantiate the kernels (rc_step.cu, rnr_step.cu).
+// translation units that instantiate the kernels (rc_step.cu,
+// rc_free_step.cu, rnr_step.cu).
 //
 // One launch advances the whole lattice by one time step.  A thread block
 // owns a segment of W = BXT * VC columns -- each of its BXT threads owns VC
@@ -21,9 +22,11 @@
 // one lane three rows ahead into a three-stage ring.  A thread reads its
 // cells' nine populations with vector shared loads (plus one scalar load for
 // the planes shifted along x) and keeps them in registers until the row
-// collides one iteration later, so a stage is free as soon as its row is read.  Cells next to a wall or a solid, and the
-// first/last column of a periodic axis, gather from global memory instead
-// (half-way bounce-back, wrap).  Results go out as vector global stores.
+// collides one iteration later, so a stage is free as soon as its row is
+// read.  A cell next to a wall or a solid reads its bounced-back
+// populations from global memory (with a mask, its open links still come
+// from the stage), as does the first/last column of a periodic x axis
+// (wrap).  Results go out as vector global stores.
 //
 // Iteration k:
 //   1. wait for the stage of row k; load each cell's nine populations into
