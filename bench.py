@@ -163,14 +163,18 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def step_kernel_hash():
+STEP_KERNEL_SOURCES = ("rc_step.cu", "rc_free_step.cu", "rnr_step.cu", "step_block.cuh",
+                       "lbm_device.cuh")
+
+
+def step_kernel_hash(csrc=None):
     """Hash of the step kernels' code (comments and whitespace left out, so
     that only a change of the code itself invalidates recorded counters)."""
     import re
+    csrc = csrc or os.path.join(ROOT, "paper_2103_02119_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("rc_step.cu", "rc_free_step.cu", "rnr_step.cu", "step_block.cuh",
-              "lbm_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2103_02119_gb300", "csrc", f)) as fh:
+    for f in STEP_KERNEL_SOURCES:
+        with open(os.path.join(csrc, f)) as fh:
             code = fh.read()
         code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
         code = re.sub(r"//[^\n]*", " ", code)

@@ -72,3 +72,26 @@ def test_max_over_ranks_single_process():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(1.5, None) == 1.5
+
+
+def test_kernel_hash_ignores_comments_not_code(tmp_path):
+    """The recorded ncu traffic is tied to the step kernels' code: a comment
+    edit keeps the hash, a code edit changes it, and the committed record
+    matches the sources as they stand."""
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    src = os.path.join(ROOT, "paper_2103_02119_gb300", "csrc")
+    for f in bench.STEP_KERNEL_SOURCES:
+        shutil.copy(os.path.join(src, f), tmp_path / f)
+    base = bench.step_kernel_hash(str(tmp_path))
+    assert base == bench.step_kernel_hash()
+    p = tmp_path / "step_block.cuh"
+    text = p.read_text()
+    p.write_text(text.replace("namespace lbm {", "namespace lbm {  // a remark\n/* a block\n remark */", 1))
+    assert bench.step_kernel_hash(str(tmp_path)) == base
+    p.write_text(text.replace("constexpr int kHalo = 4;", "constexpr int kHalo = 8;", 1))
+    assert bench.step_kernel_hash(str(tmp_path)) != base
+    with open(os.path.join(ROOT, "profiles", "rc_step_traffic.json")) as fh:
+        rec = json.load(fh)
+    assert rec["fp32"]["kernel_sha"] == base and rec["fp64"]["kernel_sha"] == base
