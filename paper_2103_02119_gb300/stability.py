@@ -30,6 +30,17 @@ def fig17_cs2(a: float, factor: float = 0.3) -> float:
     return min(1.0 / 3.0, factor * a * a)
 
 
+def largest_stable(runs) -> float:
+    """The largest value v of [(v, stable), ...] such that v and every
+    smaller value stayed stable (0 when the smallest one did not)."""
+    best = 0.0
+    for v, ok in sorted(runs):
+        if not ok:
+            break
+        best = v
+    return best
+
+
 def _run(wls, schemes, steps, check, stream):
     from .lbm import Batch
     b = Batch(wls, stream=stream, schemes=schemes)
@@ -64,15 +75,7 @@ def lid_velocity_thresholds(a_values=(1.0, 0.5, 0.3), taus=(0.51, 0.55, 0.6, 0.7
     out = {}
     for (a, tau, scheme, U), ok in zip(keys, stable):
         out.setdefault((a, tau, scheme), []).append((U, bool(ok)))
-    thr = {}
-    for key, runs in out.items():
-        best = 0.0
-        for U, ok in sorted(runs):
-            if not ok:
-                break
-            best = U
-        thr[key] = best
-    return thr
+    return {key: largest_stable(runs) for key, runs in out.items()}
 
 
 def max_reynolds(grids=((100, 200), (200, 400), (300, 600)), a=0.5, U=0.2, cs2=0.1,
@@ -92,15 +95,7 @@ def max_reynolds(grids=((100, 200), (200, 400), (300, 600)), a=0.5, U=0.2, cs2=0
     out = {}
     for (nx, ny, scheme, Re), ok in zip(keys, stable):
         out.setdefault((nx, ny, scheme), []).append((Re, bool(ok)))
-    best = {}
-    for key, runs in out.items():
-        b = 0.0
-        for Re, ok in sorted(runs):
-            if not ok:
-                break
-            b = Re
-        best[key] = b
-    return best
+    return {key: largest_stable(runs) for key, runs in out.items()}
 
 
 def main(argv=None):

@@ -158,3 +158,14 @@ def test_config2_fp32_tracks_fp64_over_10000_steps():
     _, u64, v64 = g64.moments()
     err = float(np.sqrt(((u32 - u64) ** 2 + (v32 - v64) ** 2).sum() / (u64 ** 2 + v64 ** 2).sum()))
     assert err <= 1e-5, err
+
+
+def test_lid_speed_sweep_small():
+    """A reduced lid-speed sweep (Sec. 6, Fig. 17) through the batch: at
+    tau = 0.8 on the square lattice both schemes stay stable at the low lid
+    speeds for 5,000 steps, and a repeat gives the same thresholds."""
+    from paper_2103_02119_gb300 import stability as S
+    kw = dict(a_values=(1.0,), taus=(0.8,), u_values=[0.02, 0.04, 0.06], steps=5000, check=1000)
+    t1 = S.lid_velocity_thresholds(**kw)
+    assert t1 == S.lid_velocity_thresholds(**kw)
+    assert t1[(1.0, 0.8, 0)] == 0.06 and t1[(1.0, 0.8, 1)] == 0.06
