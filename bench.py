@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-mask", action="store_true",
+                    help="skip the same cavity with a solid mask")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip the repo's own copy-bandwidth and FP64-FMA measurements")
     ap.add_argument("--no-e2e", action="store_true")
@@ -569,6 +571,24 @@ def main():
     else:
         lat.close()
 
+    # The same cavity with seeded solid rectangles (a 1.6 % cap on the solid
+    # fraction; 0.8 % of the cells at this size and seed): the mask path,
+    # whose link-mask byte adds 1 B per cell to the 72 B.
+    with_mask = None
+    if rank == 0 and not args.no_mask:
+        from paper_2103_02119_gb300 import workloads as W
+        wm = wl.with_(mask=W.random_obstacles(wl.nx, wl.ny, seed=3, coverage=0.016))
+        latm = Lattice.from_workload(wm, precision=args.precision, stream=stream)
+        nm = max(100, args.steps // 10)
+        sm, _ = time_steps(latm, torch, nm, 10, barrier)
+        latm.close()
+        bpc = BYTES_PER_CELL[args.precision] + 1
+        am = bpc * cells / (sm / nm) / 1e9
+        with_mask = {"value": cells * nm / sm / 1e6, "unit": "MLUPS", "steps": nm,
+                     "solid_fraction": float(wm.mask.mean()),
+                     "roofline": {"bound": "hbm", "achieved": am, "peak": peak, "unit": "GB/s",
+                                  "frac": am / peak, "algorithmic_bytes_per_cell": bpc}}
+
     batch = None
     if rank == 0 and not args.no_batch:
         batch = batch_throughput(torch, args.batch_count, args.batch_steps)
@@ -599,7 +619,7 @@ def main():
             "config": workload_config(args, wl), "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches,
             "clocks": clk.summary(), "fp64": fp64, "batch": batch, "small_lattice": small,
-            "warm_start": warm, "repo_peaks": peaks,
+            "warm_start": warm, "repo_peaks": peaks, "with_mask": with_mask,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
