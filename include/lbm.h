@@ -28,7 +28,9 @@
  *     into host memory synchronise it before returning.
  *   - On an error the handle stays valid and lbm_last_error describes the
  *     failure.  Invalid parameters are rejected on the host before any
- *     device work.
+ *     device work: a NULL handle, a NULL required pointer or an argument out
+ *     of its stated range gives LBM_ERR_INVALID; a failed allocation
+ *     LBM_ERR_OOM; a failed CUDA call LBM_ERR_CUDA.
  *   - A handle must not be used from two host threads at once.
  */
 #ifndef LBM_GB300_H
@@ -92,9 +94,10 @@ typedef struct {
                               step is a permutation of the state)               */
 } lbm_params;
 
-/* Fill *p with defaults: 64 x 64 periodic, a = 1, cs2 = 1/3, all omega 1,
- * no force, rho0 = 1, precision 32, both corrections on, automatic tuning,
- * RC-LBM scheme. */
+/* Fill *p with defaults: 64 x 64 periodic, a = 1, cs2 = 1/3 (the square
+ * lattice, where the corrections of Eq. 23-24 vanish), all omega 1, no
+ * force, rho0 = 1, precision 32, both corrections on, automatic tuning,
+ * RC-LBM scheme (Sec. 4).  p NULL: LBM_ERR_INVALID. */
 lbm_status lbm_params_init(lbm_params* p);
 
 /* Create a lattice.  p: parameters (copied).  solid_mask: nullable, nx*ny
@@ -124,7 +127,10 @@ lbm_status lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
  * it).  Asynchronous: the return value reports launch errors only. */
 lbm_status lbm_step(lbm_handle* h, int64_t nsteps);
 
-/* Replace the uniform body force (takes effect from the next step). */
+/* Replace the uniform body force density F (Sec. 4: it shifts the velocity
+ * to (sum f e + F/2) / rho and enters the collision through the central
+ * source moments); takes effect from the next step.  Non-finite values give
+ * LBM_ERR_INVALID. */
 lbm_status lbm_set_force(lbm_handle* h, double Fx, double Fy);
 
 /* Macroscopic fields of the current state: rho = sum_i f_i and
@@ -153,9 +159,10 @@ lbm_status lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy,
 lbm_status lbm_stress(lbm_handle* h, double* dxux, double* dyuy, double* sxy,
                       double* txx, double* tyy, double* txy, int on_device);
 
-/* Distributions f_i(x, t) of the current state (after streaming), as
- * doubles, 9*nx*ny in plane-major order f[i*nx*ny + y*nx + x]; solid cells
- * give 0.  Host or device memory as above. */
+/* Distributions f_i(x, t) of the current state (after streaming; i in the
+ * order of Eq. 2), as doubles, 9*nx*ny in plane-major order
+ * f[i*nx*ny + y*nx + x]; solid cells give 0.  Host or device memory as
+ * above. */
 lbm_status lbm_get_f(lbm_handle* h, double* f, int on_device);
 
 /* Set the current state from distributions in the layout of lbm_get_f
@@ -163,7 +170,9 @@ lbm_status lbm_get_f(lbm_handle* h, double* f, int on_device);
  * Resets the step counter and the residual reference. */
 lbm_status lbm_set_f(lbm_handle* h, const double* f, int on_device);
 
-/* FP64 global diagnostics over the fluid cells, synchronous:
+/* FP64 global diagnostics over the fluid cells, synchronous (rho and u as
+ * in Sec. 4's last step; the paper defines no global diagnostics or steady
+ * test: the sums and the residual below are this library's):
  *   out[0] mass  = sum rho; the stored values are summed exactly (fixed
  *                  point), so a permutation of the state gives the same bits
  *   out[1] sum rho u_x, out[2] sum rho u_y, out[3] sum rho |u|^2 / 2
@@ -198,7 +207,8 @@ lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]);
  * The paper has no counterpart to this entry point: it is library plumbing. */
 lbm_status lbm_diagnostics_noalloc(lbm_handle* h, double out[LBM_DIAG_COUNT]);
 
-/* Size in bytes of the raw state (checkpoint) of a handle. */
+/* Size in bytes of the raw state (checkpoint) of a handle; 0 for NULL.
+ * Checkpointing has no counterpart in the paper (library plumbing). */
 size_t lbm_state_bytes(const lbm_handle* h);
 
 /* Copy the raw device state (storage precision, internal layout) to / from
@@ -208,10 +218,11 @@ size_t lbm_state_bytes(const lbm_handle* h);
 lbm_status lbm_get_state(lbm_handle* h, void* host, size_t bytes);
 lbm_status lbm_set_state(lbm_handle* h, const void* host, size_t bytes);
 
-/* Time steps taken since the last init / set call. */
+/* Time steps taken since the last init / set call; -1 for NULL. */
 int64_t lbm_step_count(const lbm_handle* h);
 
-/* Number of kernel launches issued by lbm_step so far on this handle. */
+/* Number of kernel launches issued by lbm_step so far on this handle; -1
+ * for NULL. */
 int64_t lbm_launch_count(const lbm_handle* h);
 
 /* Message of the last error on h (or of the last failed lbm_create when h is
