@@ -5,7 +5,7 @@ A WarmNet (include/lbm_nn.h; forward, backward and Adam as CUDA kernels of
 the library) is trained on steady lid-driven cavities that the batched
 solver itself produces, and predicts, for a new instance, initial fields
 from which the unmodified scheme continues to the same steady residual.  The
-rest state stays the fallback and the judge: the warm start is measured as
+rest state stays the fallback and the yardstick: the warm start is measured as
 steps and wall time to the residual against the rest start.
 
 Instances: nx x ny = n x n cells, aspect ratio a, lid speed U, Re = U n / nu,
