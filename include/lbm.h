@@ -133,6 +133,28 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps);
  * LBM_ERR_INVALID. */
 lbm_status lbm_set_force(lbm_handle* h, double Fx, double Fy);
 
+/* Test hook for the failure path of the bounded waits (the paper has no
+ * counterpart: this is library plumbing).  A step kernel waits for each row
+ * of staged populations on an mbarrier for at most `polls` polls (default
+ * and maximum 4194304 = 2^22, far above what a copy takes); when a wait runs
+ * out, the block records it in the handle's status word, waits with the full
+ * bound for its copies still in flight, and returns, leaving the state
+ * invalid; lbm_diagnostics and lbm_diagnostics_noalloc then return
+ * LBM_ERR_TIMEOUT until lbm_init_fields, lbm_set_f or lbm_set_state gives
+ * the handle a new state.  polls = 0 makes every such wait run out at once.
+ * Takes effect from the next lbm_step.  polls outside [0, 2^22]:
+ * LBM_ERR_INVALID. */
+lbm_status lbm_set_wait_limit(lbm_handle* h, int64_t polls);
+
+/* Test hook for the allocation failure path (library plumbing, process
+ * wide, not thread-safe with concurrent allocations): nth >= 1 makes the
+ * nth device allocation the library attempts from now on fail as if the
+ * device were out of memory (no CUDA call is made for it); the entry point
+ * making it returns LBM_ERR_OOM, releases what it had allocated, and
+ * lbm_last_error names the allocation.  nth = 0 disarms the hook.  nth < 0:
+ * LBM_ERR_INVALID. */
+lbm_status lbm_debug_fail_alloc(int64_t nth);
+
 /* Macroscopic fields of the current state: rho = sum_i f_i and
  * u = (sum_i f_i e_i + F/2) / rho (Sec. 4, last step).  Each output is
  * nx*ny doubles, nullable; solid cells give 0.  Host outputs synchronise the
@@ -182,8 +204,9 @@ lbm_status lbm_set_f(lbm_handle* h, const double* f, int on_device);
  *   out[5] number of fluid cells with a non-finite rho or u
  *   out[6] step counter n
  * Returns LBM_ERR_UNSTABLE (with out filled) when out[5] > 0, and
- * LBM_ERR_TIMEOUT when a step kernel since lbm_create gave up a bounded wait
- * for its staged data. */
+ * LBM_ERR_TIMEOUT (out not written) when a step kernel gave up a bounded
+ * wait for its staged data since the state was last set (lbm_create,
+ * lbm_init_fields, lbm_set_f, lbm_set_state; see lbm_set_wait_limit). */
 lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]);
 
 /* The values of lbm_diagnostics, for callers that cannot allocate device
@@ -203,7 +226,9 @@ lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]);
  * velocity of the previous lbm_diagnostics_noalloc call, and is -1 unless
  * that call was on the same handle at a smaller step count (init and set
  * calls in between are not detected).  Calls that overlap on the GPU (other
- * streams, other threads) race on the array.
+ * streams, other threads) race on the array.  Like lbm_diagnostics it
+ * returns LBM_ERR_TIMEOUT (out not written, no residual reference taken)
+ * after a step kernel gave up a bounded wait.
  * The paper has no counterpart to this entry point: it is library plumbing. */
 lbm_status lbm_diagnostics_noalloc(lbm_handle* h, double out[LBM_DIAG_COUNT]);
 
@@ -283,7 +308,9 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
  * previous check, -1 if there was none (or no step since, or u = 0), NaN if
  * it holds non-finite values; inactive lattices keep their last value.
  * Returns LBM_ERR_UNSTABLE when a lattice holds non-finite values and
- * LBM_ERR_TIMEOUT when a step kernel gave up a bounded wait. */
+ * LBM_ERR_TIMEOUT when a step kernel gave up a bounded wait since the
+ * previous check: the lattices active in those steps then hold invalid
+ * states (re-initialise them), and the report is cleared. */
 lbm_status lbm_batch_residuals(lbm_batch* b, double* res);
 
 /* Run to a steady state: check the residuals, then repeat {step
@@ -308,6 +335,12 @@ int lbm_batch_is_active(const lbm_batch* b, int k);
  * changes the schedule only, never the results.  Default 32, 16. */
 lbm_status lbm_batch_set_shape(lbm_batch* b, int block_x, int rows_per_band);
 lbm_status lbm_batch_get_shape(const lbm_batch* b, int* block_x, int* rows_per_band);
+
+/* lbm_set_wait_limit for every lattice of the batch (a test hook): from the
+ * next step the batch kernel's row waits give up after `polls` polls; a
+ * wait that runs out is reported by lbm_batch_residuals / lbm_batch_run as
+ * LBM_ERR_TIMEOUT.  polls outside [0, 2^22]: LBM_ERR_INVALID. */
+lbm_status lbm_batch_set_wait_limit(lbm_batch* b, int64_t polls);
 
 /* Autotuner: times trial_steps (>= 1) steps of the active lattices at each
  * block_x in {32, 64, 128} and rows_per_band in {1, 2, 4, 8, 16, 32, 64} (one warm-up

@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "dev_alloc.h"
 #include "lbm.h"
 #include "lbm_launch.h"
 
@@ -17,6 +18,21 @@ using lbm::AuxParams;
 using lbm::CollConst;
 using lbm::DiagPartial;
 using lbm::KParams;
+
+// Countdown of lbm_debug_fail_alloc: when it is n > 0, the n-th device
+// allocation from then on fails.
+static std::atomic<long long> g_fail_alloc{0};
+
+cudaError_t lbm::dev_malloc(void** p, size_t bytes) {
+    long long n = g_fail_alloc.load();
+    while (n > 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 
 static unsigned long long next_handle_serial() {
     static std::atomic<unsigned long long> n{0};
@@ -41,6 +57,8 @@ struct lbm_handle {
     size_t stage_elems = 0;
     DiagPartial* part = nullptr;
     int* status = nullptr;     // device word set by a step kernel that timed out
+    bool owns_status = true;   // false for a view of a batch lattice
+    unsigned wait_limit = lbm::kWaitPolls;  // polls of the step kernel's row wait
     int diag_blocks = 0;
     int bx = 0, nbands = 0;
     int64_t steps = 0, launches = 0;
@@ -146,6 +164,7 @@ struct Geometry {
     int rstride;
     const uint8_t* lmask;
     int* status;
+    unsigned wait_limit = lbm::kWaitPolls;
 };
 
 template <typename T>
@@ -228,6 +247,7 @@ KParams<T> kparams_of(const lbm_params& q, const Geometry& g) {
     k.collide = q.scheme >= 0;
     k.raw = q.scheme == 1;
     k.status = g.status;
+    k.spin_limit = g.wait_limit;
     return k;
 }
 
@@ -256,7 +276,7 @@ AuxParams aux_of(const lbm_params& q, const Geometry& g) {
 }
 
 Geometry geometry(const lbm_handle* h) {
-    return Geometry{h->pitch, h->plane, h->rstride, h->lmask, h->status};
+    return Geometry{h->pitch, h->plane, h->rstride, h->lmask, h->status, h->wait_limit};
 }
 template <typename T>
 KParams<T> kparams(const lbm_handle* h) { return kparams_of<T>(h->p, geometry(h)); }
@@ -298,7 +318,7 @@ lbm_status ensure_stage(lbm_handle* h, size_t elems) {
     if (h->stage) cudaFree(h->stage);
     h->stage = nullptr;
     h->stage_elems = 0;
-    CK(h, cudaMalloc(&h->stage, elems * sizeof(double)), "cudaMalloc(staging)");
+    CK(h, lbm::dev_alloc(&h->stage, elems * sizeof(double)), "cudaMalloc(staging)");
     h->stage_elems = elems;
     return LBM_OK;
 }
@@ -391,10 +411,15 @@ lbm_status step_lattice(lbm_handle* h, int64_t nsteps) {
     return LBM_OK;
 }
 
-void reset_counters(lbm_handle* h) {
+// A new state: the step counter, the residual reference and the timeout
+// report start again (a batch's view leaves the batch's report alone).
+lbm_status reset_counters(lbm_handle* h) {
     h->steps = 0;
     h->have_prev = 0;
     h->prev_step = 0;
+    if (h->owns_status && h->status)
+        CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "cudaMemsetAsync(status)");
+    return LBM_OK;
 }
 
 }  // namespace
@@ -462,20 +487,20 @@ lbm_status lbm_create(const lbm_params* p, const uint8_t* solid_mask, void* cuda
     if (solid_mask) {
         std::vector<uint8_t> lm;
         h->n_fluid = build_link_mask(*p, solid_mask, h->pitch, lm);
-        CKC(cudaMalloc(&h->lmask, lm.size()), "cudaMalloc(link mask)");
+        CKC(lbm::dev_alloc(&h->lmask, lm.size()), "cudaMalloc(link mask)");
         CKC(cudaMemcpy(h->lmask, lm.data(), lm.size(), cudaMemcpyHostToDevice),
             "cudaMemcpy(link mask)");
     }
     for (int b = 0; b < 2; ++b) {
-        CKC(cudaMalloc(&h->f[b], buf_bytes(h)), "cudaMalloc(distributions)");
+        CKC(lbm::dev_alloc(&h->f[b], buf_bytes(h)), "cudaMalloc(distributions)");
         CKC(cudaMemsetAsync(h->f[b], 0, buf_bytes(h), h->stream), "cudaMemset");
     }
     int dev = 0, sms = 1;
     CKC(cudaGetDevice(&dev), "cudaGetDevice");
     CKC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
     h->diag_blocks = 2 * sms;
-    CKC(cudaMalloc(&h->part, sizeof(DiagPartial) * (h->diag_blocks + 1)), "cudaMalloc(diagnostics)");
-    CKC(cudaMalloc(&h->status, sizeof(int)), "cudaMalloc(status)");
+    CKC(lbm::dev_alloc(&h->part, sizeof(DiagPartial) * (h->diag_blocks + 1)), "cudaMalloc(diagnostics)");
+    CKC(lbm::dev_alloc(&h->status, sizeof(int)), "cudaMalloc(status)");
     CKC(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "cudaMemset");
 
     // Step kernel launch shape: one block per BX columns and per band of
@@ -539,8 +564,8 @@ lbm_status lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
                         ? lbm::launch_init<double>((double*)h->f[h->cur], a, d[0], d[1], d[2], h->stream)
                         : lbm::launch_init<float>((float*)h->f[h->cur], a, d[0], d[1], d[2], h->stream);
     CK(h, e, "init kernel");
+    if (lbm_status st = reset_counters(h); st != LBM_OK) return st;
     if (!on_device) CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    reset_counters(h);
     return LBM_OK;
 }
 
@@ -569,6 +594,23 @@ lbm_status lbm_set_force(lbm_handle* h, double Fx, double Fy) {
     h->p.Fx = Fx;
     h->p.Fy = Fy;
     drop_run_graphs(h);  // the captured steps carry the old force
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wait_limit(lbm_handle* h, int64_t polls) {
+    if (!h) return LBM_ERR_INVALID;
+    if (polls < 0 || polls > (int64_t)lbm::kWaitPolls) {
+        set_err(h, "polls must lie in [0, %u]", lbm::kWaitPolls);
+        return LBM_ERR_INVALID;
+    }
+    h->wait_limit = (unsigned)polls;
+    drop_run_graphs(h);  // the captured steps carry the old limit
+    return LBM_OK;
+}
+
+lbm_status lbm_debug_fail_alloc(int64_t nth) {
+    if (nth < 0) return LBM_ERR_INVALID;
+    g_fail_alloc.store((long long)nth);
     return LBM_OK;
 }
 
@@ -670,8 +712,8 @@ lbm_status lbm_set_f(lbm_handle* h, const double* f, int on_device) {
                         ? lbm::launch_set_f<double>((double*)h->f[h->cur], a, d[0], h->stream)
                         : lbm::launch_set_f<float>((float*)h->f[h->cur], a, d[0], h->stream);
     CK(h, e, "set_f kernel");
+    if (lbm_status st = reset_counters(h); st != LBM_OK) return st;
     if (!on_device) CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    reset_counters(h);
     return LBM_OK;
 }
 
@@ -719,7 +761,7 @@ extern "C" {
 
 lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]) {
     if (!h || !out) return LBM_ERR_INVALID;
-    if (!h->uprev) CK(h, cudaMalloc(&h->uprev, 2 * (size_t)h->N * sizeof(double)), "cudaMalloc(residual)");
+    if (!h->uprev) CK(h, lbm::dev_alloc(&h->uprev, 2 * (size_t)h->N * sizeof(double)), "cudaMalloc(residual)");
     const AuxParams a = aux(h);
     const int have = h->have_prev && h->steps > h->prev_step;
     cudaError_t e = h->p.precision == 64
@@ -780,8 +822,8 @@ lbm_status lbm_set_state(lbm_handle* h, const void* host, size_t bytes) {
     }
     CK(h, cudaMemcpyAsync(h->f[h->cur], host, bytes, cudaMemcpyHostToDevice, h->stream),
        "cudaMemcpyAsync(H2D)");
+    if (lbm_status st = reset_counters(h); st != LBM_OK) return st;
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    reset_counters(h);
     return LBM_OK;
 }
 
@@ -874,7 +916,15 @@ extern "C" lbm_status lbm_diagnostics_noalloc(lbm_handle* h, double out[LBM_DIAG
     CK(h, cudaMemcpyAsync(&r, part + h->diag_blocks, sizeof(r), cudaMemcpyDeviceToHost,
                           h->stream),
        "cudaMemcpyAsync(D2H)");
+    int kstatus = 0;
+    CK(h, cudaMemcpyAsync(&kstatus, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+       "cudaMemcpyAsync(D2H)");
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (kstatus) {
+        // the state is not valid: no values, and no residual reference taken
+        set_err(h, "a step kernel gave up waiting for its staged data (status %d)", kstatus);
+        return LBM_ERR_TIMEOUT;
+    }
     out[0] = fixed_to_double(r.limb) + (double)h->n_fluid * h->p.rho0;
     out[1] = r.mx;
     out[2] = r.my;
@@ -1104,6 +1154,7 @@ void make_view(lbm_batch* b, int k, lbm_handle& h) {
     h.part = b->d_diag;
     h.diag_blocks = b->diag_blocks;
     h.status = b->status;
+    h.owns_status = false;
     h.steps = b->steps[k];
 }
 
@@ -1215,21 +1266,21 @@ lbm_status lbm_batch_create(const lbm_params* params, int count,
     BCKC(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev),
          "cudaDeviceGetAttribute");
     BCKC(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
-    BCKC(cudaMalloc(&b->fbase, fl * sizeof(float)), "cudaMalloc(distributions)");
-    BCKC(cudaMalloc(&b->mbase, ml), "cudaMalloc(link masks)");
-    BCKC(cudaMalloc(&b->ubase, ul * sizeof(double)), "cudaMalloc(residual fields)");
+    BCKC(lbm::dev_alloc(&b->fbase, fl * sizeof(float)), "cudaMalloc(distributions)");
+    BCKC(lbm::dev_alloc(&b->mbase, ml), "cudaMalloc(link masks)");
+    BCKC(lbm::dev_alloc(&b->ubase, ul * sizeof(double)), "cudaMalloc(residual fields)");
     BCKC(cudaMemsetAsync(b->fbase, 0, fl * sizeof(float), b->stream), "cudaMemset");
     BCKC(cudaMemsetAsync(b->ubase, 0, ul * sizeof(double), b->stream), "cudaMemset");
-    BCKC(cudaMalloc(&b->status, sizeof(int)), "cudaMalloc(status)");
+    BCKC(lbm::dev_alloc(&b->status, sizeof(int)), "cudaMalloc(status)");
     BCKC(cudaMemsetAsync(b->status, 0, sizeof(int), b->stream), "cudaMemset");
-    BCKC(cudaMalloc(&b->d_lat, sizeof(BatchLattice<float>) * count), "cudaMalloc(lattice table)");
-    BCKC(cudaMalloc(&b->d_aux, sizeof(BatchAux) * count), "cudaMalloc(lattice table)");
-    BCKC(cudaMalloc(&b->d_list, sizeof(int) * b->h_list.size()), "cudaMalloc(work list)");
+    BCKC(lbm::dev_alloc(&b->d_lat, sizeof(BatchLattice<float>) * count), "cudaMalloc(lattice table)");
+    BCKC(lbm::dev_alloc(&b->d_aux, sizeof(BatchAux) * count), "cudaMalloc(lattice table)");
+    BCKC(lbm::dev_alloc(&b->d_list, sizeof(int) * b->h_list.size()), "cudaMalloc(work list)");
     for (int k = 0; k < count; ++k) b->has_scheme[params[k].scheme == 1 ? 1 : 0] = true;
-    BCKC(cudaMalloc(&b->d_part, sizeof(ResPartial) * (size_t)chunks), "cudaMalloc(residual sums)");
-    BCKC(cudaMalloc(&b->d_res, sizeof(ResPartial) * (size_t)count), "cudaMalloc(residual sums)");
+    BCKC(lbm::dev_alloc(&b->d_part, sizeof(ResPartial) * (size_t)chunks), "cudaMalloc(residual sums)");
+    BCKC(lbm::dev_alloc(&b->d_res, sizeof(ResPartial) * (size_t)count), "cudaMalloc(residual sums)");
     b->diag_blocks = 2 * b->sms;
-    BCKC(cudaMalloc(&b->d_diag, sizeof(DiagPartial) * (b->diag_blocks + 1)),
+    BCKC(lbm::dev_alloc(&b->d_diag, sizeof(DiagPartial) * (b->diag_blocks + 1)),
          "cudaMalloc(diagnostics)");
 
     std::vector<uint8_t> zero, lm;
@@ -1337,6 +1388,22 @@ lbm_status lbm_batch_set_shape(lbm_batch* b, int block_x, int rows_per_band) {
     return set_shape(b, block_x, rows_per_band);
 }
 
+lbm_status lbm_batch_set_wait_limit(lbm_batch* b, int64_t polls) {
+    if (!b) return LBM_ERR_INVALID;
+    if (polls < 0 || polls > (int64_t)lbm::kWaitPolls) {
+        bset_err(b, "polls must lie in [0, %u]", lbm::kWaitPolls);
+        return LBM_ERR_INVALID;
+    }
+    for (int k = 0; k < b->count; ++k) {
+        b->geo[k].wait_limit = (unsigned)polls;
+        b->lat[k].kp.spin_limit = (unsigned)polls;
+    }
+    BCK(b, cudaMemcpyAsync(b->d_lat, b->lat.data(), sizeof(BatchLattice<float>) * b->count,
+                           cudaMemcpyHostToDevice, b->stream),
+        "cudaMemcpyAsync(lattice table)");
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_get_shape(const lbm_batch* b, int* block_x, int* rows_per_band) {
     if (!b) return LBM_ERR_INVALID;
     if (block_x) *block_x = b->bx;
@@ -1406,6 +1473,10 @@ lbm_status lbm_batch_residuals(lbm_batch* b, double* res) {
         "cudaMemcpyAsync(D2H)");
     BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
     if (kstatus) {
+        // reported once: the word is cleared, and the lattices that were
+        // active in the steps since the last check hold invalid states
+        BCK(b, cudaMemsetAsync(b->status, 0, sizeof(int), b->stream), "cudaMemsetAsync(status)");
+        BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
         bset_err(b, "a batch step kernel gave up waiting for its staged data (status %d)", kstatus);
         return LBM_ERR_TIMEOUT;
     }

@@ -63,6 +63,7 @@ struct KParams {
     int collide;              // 0: streaming and bounce-back only
     int raw;                  // 1: raw-moment collision (RNR-LBM, Sec. 3)
     int forced;               // a body force is set
+    unsigned spin_limit;      // polls of a bounded wait for staged rows
     T a, iah, iah2, cs2, rho0;  // a, 1/(2a), 1/(2a^2), c_s^2, rho0
     T wall_u[4][2];
     const uint8_t* __restrict__ lmask;  // per-cell link mask (nullable)

@@ -7,6 +7,10 @@
 
 namespace lbm {
 
+// Polls of the step kernels' bounded mbarrier waits (the default of
+// KParams::spin_limit and the bound of the drain after a wait ran out).
+constexpr unsigned kWaitPolls = 1u << 22;
+
 // Fixed-point accumulator of the exact mass: value = sum_k limb[k] 2^(24k - 144).
 constexpr int kMassLimbs = 8;
 constexpr int kMassShift = 144;

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "lbm_nn.h"
+#include "dev_alloc.h"
 
 namespace {
 
@@ -842,9 +843,9 @@ lbm_status lbm_nn_create(int levels, const int* channels, int max_batch, int hei
         maxw = conv_wsize(c) > maxw ? conv_wsize(c) : maxw;
     }
     nn->pfloats = pf;
-    NCKC(cudaMalloc(&nn->pbuf, pf * sizeof(float)), "cudaMalloc(parameters)");
+    NCKC(lbm::dev_alloc(&nn->pbuf, pf * sizeof(float)), "cudaMalloc(parameters)");
     NCKC(cudaMemsetAsync(nn->pbuf, 0, pf * sizeof(float), nn->stream), "cudaMemset");
-    NCKC(cudaMalloc(&nn->wbuf, wb * sizeof(bf16)), "cudaMalloc(weights)");
+    NCKC(lbm::dev_alloc(&nn->wbuf, wb * sizeof(bf16)), "cudaMalloc(weights)");
     {
         float* q = nn->pbuf;
         bf16* r = nn->wbuf;
@@ -869,7 +870,7 @@ lbm_status lbm_nn_create(int levels, const int* channels, int max_batch, int hei
         ab += 2 * ((e * sizeof(bf16) + 255) / 256 * 256);
         maxt = e > maxt ? e : maxt;
     }
-    NCKC(cudaMalloc(&nn->abuf, ab), "cudaMalloc(activations)");
+    NCKC(lbm::dev_alloc(&nn->abuf, ab), "cudaMalloc(activations)");
     NCKC(cudaMemsetAsync(nn->abuf, 0, ab, nn->stream), "cudaMemset");
     {
         unsigned char* q = nn->abuf;
@@ -881,16 +882,16 @@ lbm_status lbm_nn_create(int levels, const int* channels, int max_batch, int hei
             q += e;
         }
     }
-    NCKC(cudaMalloc(&nn->scratch, maxt * sizeof(bf16)), "cudaMalloc(scratch)");
+    NCKC(lbm::dev_alloc(&nn->scratch, maxt * sizeof(bf16)), "cudaMalloc(scratch)");
     const long long Pmax = (long long)nn->nb * nn->H * nn->W;
     const long long splits = (Pmax + kSplitPixels - 1) / kSplitPixels;
     nn->part_floats = (size_t)splits * maxw;
-    NCKC(cudaMalloc(&nn->part, nn->part_floats * sizeof(float)), "cudaMalloc(partials)");
-    NCKC(cudaMalloc(&nn->dpart, 1025 * sizeof(double)), "cudaMalloc(loss)");
-    NCKC(cudaMalloc(&nn->xin, Pmax * 4 * sizeof(float)), "cudaMalloc(inputs)");
-    NCKC(cudaMalloc(&nn->tgt, Pmax * 3 * sizeof(float)), "cudaMalloc(targets)");
-    NCKC(cudaMalloc(&nn->fl, Pmax), "cudaMalloc(fluid)");
-    NCKC(cudaMalloc(&nn->yout, Pmax * 3 * sizeof(float)), "cudaMalloc(outputs)");
+    NCKC(lbm::dev_alloc(&nn->part, nn->part_floats * sizeof(float)), "cudaMalloc(partials)");
+    NCKC(lbm::dev_alloc(&nn->dpart, 1025 * sizeof(double)), "cudaMalloc(loss)");
+    NCKC(lbm::dev_alloc(&nn->xin, Pmax * 4 * sizeof(float)), "cudaMalloc(inputs)");
+    NCKC(lbm::dev_alloc(&nn->tgt, Pmax * 3 * sizeof(float)), "cudaMalloc(targets)");
+    NCKC(lbm::dev_alloc(&nn->fl, Pmax), "cudaMalloc(fluid)");
+    NCKC(lbm::dev_alloc(&nn->yout, Pmax * 3 * sizeof(float)), "cudaMalloc(outputs)");
 #undef NCKC
     // He-normal initial weights (host generator), zero biases
     std::vector<float> params(lbm_nn_param_count(nn));

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm.h"
+#include "dev_alloc.h"
 
 namespace {
 
@@ -70,8 +71,8 @@ extern "C" lbm_status lbm_peak_copy_gbs(size_t bytes, int iters, void* stream, d
     if (sms <= 0) return LBM_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     void *a = nullptr, *b = nullptr;
-    cudaError_t e = cudaMalloc(&a, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&b, bytes);
+    cudaError_t e = lbm::dev_alloc(&a, bytes);
+    if (e == cudaSuccess) e = lbm::dev_alloc(&b, bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(a, 0, bytes, s);
     float ms = 0.0f;
     if (e == cudaSuccess) {
@@ -99,7 +100,7 @@ extern "C" lbm_status lbm_peak_fp64_gflops(int iters, void* stream, double* gflo
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int grid = sms * 4, block = 256;
     double* out = nullptr;
-    cudaError_t e = cudaMalloc(&out, (size_t)grid * block * sizeof(double));
+    cudaError_t e = lbm::dev_alloc(&out, (size_t)grid * block * sizeof(double));
     float ms = 0.0f;
     if (e == cudaSuccess)
         e = time_launches(

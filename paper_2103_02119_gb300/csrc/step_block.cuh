@@ -56,7 +56,10 @@ namespace {
 
 constexpr int kStages = 3;              // stage ring depth (copies run 3 rows ahead)
 constexpr int kHalo = 4;                // staged columns on each side of a segment
-constexpr unsigned kSpinLimit = 1u << 22;
+// Polls of a bounded wait: the drain of the copies in flight always uses
+// kSpinLimit; the wait for a row's data uses the lattice's spin_limit (the
+// same by default; a test may set it lower to make that wait run out).
+constexpr unsigned kSpinLimit = kWaitPolls;
 
 __device__ __forceinline__ unsigned smem_u32(const void* ptr) {
     return (unsigned)__cvta_generic_to_shared(ptr);
@@ -82,9 +85,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait; false when it ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-    for (unsigned n = 0; n < kSpinLimit; ++n)
+// Bounded wait of at most `limit` polls; false when it ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity,
+                                          unsigned limit = kSpinLimit) {
+    for (unsigned n = 0; n < limit; ++n)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -150,12 +154,37 @@ __device__ __forceinline__ void mbar_inval(unsigned bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// The collision's constants, read afresh at each use from a parameter block
+// in shared memory (a lattice of a batch): one broadcast load per constant
+// (the low half of its lane pair, duplicated), which the compiler may not
+// hoist out of the row loop, so that the constants occupy registers only
+// during the collision, as the constant-bank operands of a single-lattice
+// kernel do.
+__device__ __forceinline__ CollConst<float> fresh_consts(const CollConst<float>& src) {
+    constexpr int n = sizeof(CollConst<float>) / sizeof(float2);
+    static_assert(sizeof(CollConst<float>) % sizeof(float2) == 0, "constants are lane pairs");
+    const volatile float* s = reinterpret_cast<const volatile float*>(&src);
+    CollConst<float> c;
+    float2* d = reinterpret_cast<float2*>(&c);
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const float v = s[2 * i];
+        d[i] = make_float2(v, v);
+    }
+    return c;
+}
+__device__ __forceinline__ CollConst<double> fresh_consts(const CollConst<double>& src) {
+    return src;
+}
+
 // One block's work: segment `seg` of columns and row band `band` (of nbands)
 // of one lattice, from fin to fout.  smem: step_smem_bytes<T, BXT>() bytes.
 // Returns false when a wait ran out (the block must stop).
 // PT: KParams<T> or const KParams<T>& (a kernel parameter, or the copy in
-// shared memory of a lattice of a batch).
-template <typename T, bool MASK, int BXT, typename I, int SCH, typename PT = KParams<T>>
+// shared memory of a lattice of a batch).  SMEMP: the parameters are in
+// shared memory (the collision's constants are then re-read at each use).
+template <typename T, bool MASK, int BXT, typename I, int SCH, typename PT = KParams<T>,
+          bool SMEMP = false>
 __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restrict__ fout,
                                            const PT p, int nbands, int seg, int band,
                                            unsigned char* smem) {
@@ -397,7 +426,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         const int r = rfirst + dir * k;
         const int s = k % kStages;
         const int slot = k & 3;
-        const bool to = !mbar_wait(bar0 + 8u * s, (unsigned)((k / kStages) & 1));
+        const bool to = !mbar_wait(bar0 + 8u * s, (unsigned)((k / kStages) & 1), p.spin_limit);
 
         // 1. density of row r and of the two halo columns
         const bool rv = row_valid(r);
@@ -526,8 +555,8 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                     const float2 D = make_float2(dp[0], dp[1]);
                     const float2 Gx = make_float2(dxr[0], dxr[1]), Gy = make_float2(dyr[0], dyr[1]);
                     const float2 R = (SCH == 1 || (SCH == 2 && p.raw))
-                                         ? collide_raw<float>(CollConst<float>(p.cc), F, D, Gx, Gy)
-                                         : collide<float, SCH != 3>(CollConst<float>(p.cc), F, D, Gx, Gy);
+                                         ? collide_raw<float>(SMEMP ? fresh_consts(p.cc) : CollConst<float>(p.cc), F, D, Gx, Gy)
+                                         : collide<float, SCH != 3>(SMEMP ? fresh_consts(p.cc) : CollConst<float>(p.cc), F, D, Gx, Gy);
                     rho[0] = R.x;
                     rho[1] = R.y;
                     // A solid cell keeps its zeros.  Without a mask the only

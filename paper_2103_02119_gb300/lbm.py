@@ -74,6 +74,8 @@ def _load():
     L.lbm_init_fields.argtypes = [_P, _P, _P, _P, ctypes.c_int]
     L.lbm_step.argtypes = [_P, ctypes.c_int64]
     L.lbm_set_force.argtypes = [_P, ctypes.c_double, ctypes.c_double]
+    L.lbm_set_wait_limit.argtypes = [_P, ctypes.c_int64]
+    L.lbm_debug_fail_alloc.argtypes = [ctypes.c_int64]
     L.lbm_moments.argtypes = [_P, _P, _P, _P, ctypes.c_int]
     L.lbm_get_f.argtypes = [_P, _P, ctypes.c_int]
     L.lbm_stress.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int]
@@ -103,6 +105,7 @@ def _load():
     L.lbm_batch_set_active.argtypes = [_P, ctypes.c_int, ctypes.c_int]
     L.lbm_batch_is_active.argtypes = [_P, ctypes.c_int]
     L.lbm_batch_set_shape.argtypes = [_P, ctypes.c_int, ctypes.c_int]
+    L.lbm_batch_set_wait_limit.argtypes = [_P, ctypes.c_int64]
     _IP = ctypes.POINTER(ctypes.c_int)
     L.lbm_batch_get_shape.argtypes = [_P, _IP, _IP]
     L.lbm_batch_tune.argtypes = [_P, ctypes.c_int, _IP, _IP]
@@ -215,6 +218,14 @@ def lbm_step(h, nsteps: int):
 
 def lbm_set_force(h, Fx: float, Fy: float):
     _check(lib.lbm_set_force(h, float(Fx), float(Fy)), h)
+
+
+def lbm_set_wait_limit(h, polls: int):
+    _check(lib.lbm_set_wait_limit(h, int(polls)), h)
+
+
+def lbm_debug_fail_alloc(nth: int):
+    _check(lib.lbm_debug_fail_alloc(int(nth)), None)
 
 
 def lbm_moments(h, N, rho=None, ux=None, uy=None):
@@ -422,6 +433,10 @@ def lbm_batch_is_active(b, k) -> int:
 
 def lbm_batch_set_shape(b, block_x, rows_per_band):
     _bcheck(lib.lbm_batch_set_shape(b, int(block_x), int(rows_per_band)), b)
+
+
+def lbm_batch_set_wait_limit(b, polls: int):
+    _bcheck(lib.lbm_batch_set_wait_limit(b, int(polls)), b)
 
 
 def lbm_batch_get_shape(b):

@@ -167,3 +167,24 @@ def test_peak_probes_reject_bad_arguments_on_host(L):
     assert L.lib.lbm_peak_fp64_gflops(0, None, ctypes.byref(out)) == L.LBM_ERR_INVALID
     assert L.lib.lbm_peak_fp64_gflops(10, None, None) == L.LBM_ERR_INVALID
     assert out.value == -1.0
+
+
+def test_allocation_failure_hook_gives_oom_on_the_host(L):
+    """lbm_debug_fail_alloc(1) fails the next device allocation before any
+    CUDA call: lbm_create's first allocation is a population buffer, so it
+    returns LBM_ERR_OOM, frees what it holds and names the allocation."""
+    p = L.lbm_params_init()
+    L.lbm_debug_fail_alloc(1)
+    with pytest.raises(L.LbmError) as e:
+        L.lbm_create(p)
+    assert e.value.status == L.LBM_ERR_OOM
+    assert "distributions" in str(e.value)
+    assert "distributions" in L.lbm_last_error(None)
+    # the hook fired once and is disarmed; bad arguments are rejected
+    assert L.lib.lbm_debug_fail_alloc(-1) == L.LBM_ERR_INVALID
+    assert L.lib.lbm_debug_fail_alloc(0) == L.LBM_OK
+
+
+def test_wait_limit_rejects_bad_arguments_on_host(L):
+    assert L.lib.lbm_set_wait_limit(None, 10) == L.LBM_ERR_INVALID
+    assert L.lib.lbm_batch_set_wait_limit(None, 10) == L.LBM_ERR_INVALID

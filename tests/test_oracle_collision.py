@@ -198,3 +198,89 @@ def test_shear_stress_of_steady_channels_is_linear(orc):
         assert np.abs(prof - exact).max() < 0.02 * np.abs(exact).max(), (a, prof, exact)
         assert np.abs(txx).max() < 1e-2 * np.abs(exact).max()
         assert np.abs(tyy).max() < 1e-2 * np.abs(exact).max()
+
+
+# ---- RNR-LBM (Sec. 3): raw equilibria (Eq. 12) and raw sources (Eq. 13) ----
+#
+# The raw-moment scheme's source and equilibrium moments must be the raw
+# moments of the central-moment quantities of Sec. 4 seen from the lab frame.
+# A source with central moments (0, Fx, Fy, 0, ..., 0) about u has, for each
+# basis polynomial P of Eq. 3, the raw moment sum_i S_i P(e_i) =
+# F . grad P(u) (Taylor-expand P(e_i) = P(u + c_i) in c_i = e_i - u: every
+# term is a central basis monomial and only the first-order ones carry a
+# source).  The raw equilibrium is the raw moment of the product-form f^eq.
+# Both are evaluated here in exact rational arithmetic, independently of the
+# oracle's typed formulas.
+
+def _P(k, x, y):
+    return [1, x, y, x * x + y * y, x * x - y * y, x * y, x * x * y, x * y * y,
+            x * x * y * y][k]
+
+
+def _gradP(k, x, y):
+    return [(0, 0), (1, 0), (0, 1), (2 * x, 2 * y), (2 * x, -2 * y), (y, x),
+            (2 * x * y, x * x), (y * y, 2 * x * y), (2 * x * y * y, 2 * x * x * y)][k]
+
+
+def _exact_feq(a, cs2, rho, ux, uy):
+    def px(e, u):
+        return 1 - cs2 - u * u if e == 0 else (cs2 + u * u + e * u) / 2
+    def py(e, u):
+        return 1 - (cs2 + u * u) / (a * a) if e == 0 else (cs2 + u * u + e * a * u) / (2 * a * a)
+    return [rho * px(int(EX[i]), ux) * py(int(EY[i]), uy) for i in range(9)]
+
+
+def _rnr_case(seed):
+    from fractions import Fraction as Q
+    rng = np.random.default_rng(100 + seed)
+    a = Q(int(rng.integers(2, 9)), 4)                       # 0.5 .. 2
+    cs2 = min(a * a, Q(1)) * Q(int(rng.integers(1, 6)), 10)  # below min(1, a^2)
+    f = [Q(int(v), 1000) for v in rng.integers(20, 300, 9)]
+    Fx, Fy = (Q(int(v), 20000) for v in rng.integers(-200, 201, 2))
+    rho = sum(f)
+    jx = sum(fi * int(EX[i]) for i, fi in enumerate(f))
+    jy = sum(fi * int(EY[i]) * a for i, fi in enumerate(f))
+    ux, uy = (jx + Fx / 2) / rho, (jy + Fy / 2) / rho
+    return a, cs2, f, Fx, Fy, rho, ux, uy
+
+
+def _raw_after(orc, a, cs2, f, Fx, Fy, om):
+    p = params(orc, float(a), float(cs2), om, float(Fx), float(Fy), iso=0, gi=0, scheme="rnr")
+    ft, _ = orc.collide_cell(p, np.array([float(v) for v in f]))
+    return [sum(ft[i] * float(_P(k, EX[i], EY[i] * float(a))) for i in range(9))
+            for k in range(9)]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_rnr_source_moments_are_the_lab_frame_central_source(orc, seed):
+    """omega_5..8 = 0 leaves m~_k = m_k + Phi_k: Phi_5..8 of Eq. 13 against
+    F . grad P(u); omega_3 = omega_4 = 1 (corrections off) leaves
+    m~_k = m^eq_k + Phi_k / 2: Phi_3, Phi_4."""
+    a, cs2, f, Fx, Fy, rho, ux, uy = _rnr_case(seed)
+    om = [1, 1, 1, 1, 1, 0, 0, 0, 0]
+    got = _raw_after(orc, a, cs2, f, Fx, Fy, om)
+    feq = _exact_feq(a, cs2, rho, ux, uy)
+    for k in range(3, 9):
+        gx, gy = _gradP(k, ux, uy)
+        phi = Fx * gx + Fy * gy
+        m = sum(fi * _P(k, int(EX[i]), int(EY[i]) * a) for i, fi in enumerate(f))
+        meq = sum(v * _P(k, int(EX[i]), int(EY[i]) * a) for i, v in enumerate(feq))
+        want = m + phi if k >= 5 else meq + phi / 2
+        assert abs(got[k] - float(want)) <= 1e-13 * max(1.0, abs(float(want))), (k, got[k], want)
+        # the source term is far above the tolerance: a wrong coefficient shows
+        assert abs(float(phi)) > 1e-7 or k == 5
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_rnr_raw_equilibria_are_the_product_form_moments(orc, seed):
+    """Every omega = 1 (corrections off): m~_k = m^eq_k + Phi_k / 2 for every
+    k, with m^eq_k the raw moments of the product-form equilibrium (Eq. 12
+    with the reading of its last entry) and Phi_k = F . grad P_k(u)."""
+    a, cs2, f, Fx, Fy, rho, ux, uy = _rnr_case(seed)
+    got = _raw_after(orc, a, cs2, f, Fx, Fy, [1.0] * 9)
+    feq = _exact_feq(a, cs2, rho, ux, uy)
+    for k in range(9):
+        gx, gy = _gradP(k, ux, uy)
+        meq = sum(v * _P(k, int(EX[i]), int(EY[i]) * a) for i, v in enumerate(feq))
+        want = meq + (Fx * gx + Fy * gy) / 2
+        assert abs(got[k] - float(want)) <= 1e-13 * max(1.0, abs(float(want))), (k, got[k], want)
