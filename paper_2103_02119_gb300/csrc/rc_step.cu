@@ -7,7 +7,7 @@ namespace lbm {
 
 // Resident 128-thread blocks per SM the batch kernel is bounded for.
 #ifndef LBM_BATCH_BLOCKS
-#define LBM_BATCH_BLOCKS 5
+#define LBM_BATCH_BLOCKS 4
 #endif
 constexpr int kBatchBlocks128 = LBM_BATCH_BLOCKS;
 
