@@ -58,7 +58,7 @@ typedef enum {
 } lbm_status;
 
 /* Number of doubles written by lbm_diagnostics. */
-#define LBM_DIAG_COUNT 7
+#define LBM_DIAG_COUNT 8
 
 typedef struct {
     int32_t nx, ny;        /* cells along x and y, each >= 3                    */
@@ -198,11 +198,23 @@ lbm_status lbm_set_f(lbm_handle* h, const double* f, int on_device);
  *   out[0] mass  = sum rho; the stored values are summed exactly (fixed
  *                  point), so a permutation of the state gives the same bits
  *   out[1] sum rho u_x, out[2] sum rho u_y, out[3] sum rho |u|^2 / 2
- *   out[4] steady residual sqrt(sum |u(n) - u(m)|^2) / ((n - m) sqrt(sum
- *          |u(n)|^2)) against the state m of the previous call, or -1 when
- *          there is no previous call (or n == m)
+ *   out[4] steady residual sqrt(sum |ubar(n) - ubar(m)|^2) / ((n - m)
+ *          sqrt(sum |ubar(n)|^2)) against the state m of the previous call,
+ *          or -1 when there is no previous call (or n == m), where
+ *          ubar(n) = (u(n) + u(n-1)) / 2 is the mean velocity of the last
+ *          two steps (u(n) alone before the first step since the state was
+ *          set).  The scheme carries two exact invariants besides the mass,
+ *          the staggered momenta sum (-1)^(x+n) rho u_x and
+ *          sum (-1)^(y+n) rho u_y (streaming with half-way bounce-back moves
+ *          their carriers one cell and flips their sign, the collision
+ *          conserves momentum): motion along them alternates every step and
+ *          never decays, a residual between states an even number of steps
+ *          apart is blind to it, and the two-step mean cancels it
  *   out[5] number of fluid cells with a non-finite rho or u
  *   out[6] step counter n
+ *   out[7] step-to-step change sqrt(sum |u(n) - u(n-1)|^2) / sqrt(sum
+ *          |ubar(n)|^2), which such alternating motion keeps away from zero;
+ *          -1 before the first step since the state was set
  * Returns LBM_ERR_UNSTABLE (with out filled) when out[5] > 0, and
  * LBM_ERR_TIMEOUT (out not written) when a step kernel gave up a bounded
  * wait for its staged data since the state was last set (lbm_create,
@@ -304,8 +316,9 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
 
 /* Steady residual of every lattice, synchronous: res (count doubles,
  * nullable) gets, for each active lattice, the residual of lbm_diagnostics'
- * out[4] (FP64 sums over its fluid cells) against its velocity at its
- * previous check, -1 if there was none (or no step since, or u = 0), NaN if
+ * out[4] (FP64 sums over its fluid cells, on the two-step mean velocity)
+ * against its mean velocity at its previous check, -1 if there was none (or
+ * no step since, or u = 0), NaN if
  * it holds non-finite values; inactive lattices keep their last value.
  * Returns LBM_ERR_UNSTABLE when a lattice holds non-finite values and
  * LBM_ERR_TIMEOUT when a step kernel gave up a bounded wait since the

@@ -16,13 +16,26 @@
  *            x = avgpool2(x) unless l = L-1
  *   decoder, l = L-2 .. 0: x = upsample2(x); x = relu(conv(x));
  *            x = x + e[l]; x = relu(conv(x))
- *   output:  y = conv(x) (c[0] -> 3 channels)
+ *   output:  y = conv(x) (c[0] -> 3 channels), then the fixed output stage
+ *            out = unstagger(smooth(y))
  * A convolution computes out(y, x) = b + sum_{dy,dx} in(y+dy-1, x+dx-1)
  * W[dy][dx] with zero padding.  Inputs have 4 channels, outputs 3.
+ * Output stage (no parameters; a cell is fluid where input channel 0, the
+ * solid flag, is below 1/2): smooth applies [1, 2, 1] / 4 along x and then
+ * along y, with solid cells and cells outside the grid taken as 0, and sets
+ * solid cells to 0; unstagger removes from output channel 1 (u_x) its
+ * component along (-1)^x and from channel 2 (u_y) its component along
+ * (-1)^y over each instance's fluid cells.  The lattice Boltzmann scheme
+ * keeps the staggered momenta sum (-1)^(x+n) rho u_x and
+ * sum (-1)^(y+n) rho u_y exactly (lbm.h, lbm_diagnostics), so a warm start
+ * carrying them would settle on a different state from the rest start; the
+ * output stage gives predictions none.  Both maps are self-adjoint; the
+ * backward pass applies them in reverse order.
  *
  * Storage: activations BF16 NHWC with channels padded to a multiple of 8;
  * weights kept as FP32 masters with BF16 copies; gradients of activations
- * BF16, of parameters FP32.  Loss: sum over fluid cells (fluid != 0) of the
+ * BF16, of parameters FP32; the output stage, its result and the loss
+ * gradient FP32.  Loss: sum over fluid cells (fluid != 0) of the
  * squared output error, divided by 3 x the number of fluid cells.
  *
  * Parameter vector (lbm_nn_get_params / set_params / gradients): for each

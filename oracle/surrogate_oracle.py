@@ -14,7 +14,8 @@ c[0] .. c[L-1]:
   decoder, level l = L-2 .. 0:
       x = upsample2(x); x = relu(conv(x)) (c[l+1] -> c[l]);
       x = x + skip[l]; x = relu(conv(x))
-  output: y = conv(x) (c[0] -> 3 channels, no activation)
+  output: y = conv(x) (c[0] -> 3 channels, no activation), then the fixed
+          output stage p = unstagger(smooth(y)) below
 
 Arrays are NHWC (n, h, w, c); a convolution has weights (3, 3, cin, cout)
 (tap row, tap column, input channel, output channel) and a bias (cout,), and
@@ -22,12 +23,27 @@ computes out(y, x) = b + sum_{dy,dx} in(y + dy - 1, x + dx - 1) W[dy, dx]
 with zeros outside the grid.  avgpool2 averages 2x2 blocks; upsample2
 repeats each value into a 2x2 block.
 
+Output stage (fixed, no parameters; fluid = input channel 0 below 1/2):
+smooth() applies [1, 2, 1] / 4 along x and then along y to each channel,
+taking the values at solid cells and outside the grid as 0, and sets solid
+cells to 0; unstagger() removes from channel 1 (u_x) its component along
+(-1)^x and from channel 2 (u_y) its component along (-1)^y over the fluid
+cells of each instance (an orthogonal projection).  The lattice Boltzmann
+scheme keeps the staggered momenta sum (-1)^(x+n) rho u_x and
+sum (-1)^(y+n) rho u_y exactly, so a start that carries them never reaches
+the steady state of a start from rest; the smoothing removes the grid-scale
+content that feeds them and the projection sets what is left to zero.  Both
+maps are self-adjoint, so the backward pass applies them again (in reverse
+order).
+
 With ``bf16_storage=True`` the weights, every stored activation and every
 stored activation gradient are rounded to bfloat16 (round to nearest even)
 where the CUDA kernels store them -- the inputs, each layer's output, the
-loss gradient, each input gradient of a convolution, of an upsampling and
+gradient of the last convolution's output (after the output stage's
+backward pass), each input gradient of a convolution, of an upsampling and
 of a pooling (together with the skip gradient it joins) -- while sums stay
-in FP64 and parameter gradients are not rounded.
+in FP64, and the output stage, its result, the loss gradient and the
+parameter gradients are not rounded (the kernels keep them in FP32).
 
 Loss: L = sum_m fluid(m) sum_c (y - t)^2 / (3 sum_m fluid(m)), over all
 cells m of the batch; solid cells do not count.
@@ -94,6 +110,48 @@ def upsample2_backward(gy):
     return gy[:, 0::2, 0::2] + gy[:, 1::2, 0::2] + gy[:, 0::2, 1::2] + gy[:, 1::2, 1::2]
 
 
+def fluid_of_input(x):
+    """Fluid flag per cell from the input planes (channel 0: solid flag)."""
+    return np.asarray(x)[..., 0] < 0.5
+
+
+def smooth(y, fluid):
+    """[1, 2, 1] / 4 along x, then along y, of every channel; solid cells and
+    cells outside the grid count as 0, and solid cells are set to 0."""
+    m = fluid[..., None].astype(np.float64)
+    g = y * m
+    p = np.pad(g, ((0, 0), (0, 0), (1, 1), (0, 0)))
+    g = 0.25 * p[:, :, :-2] + 0.5 * p[:, :, 1:-1] + 0.25 * p[:, :, 2:]
+    p = np.pad(g, ((0, 0), (1, 1), (0, 0), (0, 0)))
+    g = 0.25 * p[:, :-2] + 0.5 * p[:, 1:-1] + 0.25 * p[:, 2:]
+    return g * m
+
+
+def unstagger(y, fluid):
+    """Channel 1 minus its projection on (-1)^x, channel 2 minus its
+    projection on (-1)^y, over the fluid cells of each instance."""
+    n, h, w, _ = y.shape
+    yy, xx = np.mgrid[0:h, 0:w]
+    out = np.array(y, dtype=np.float64, copy=True)
+    for k in range(n):
+        m = fluid[k].astype(np.float64)
+        nf = m.sum()
+        if nf == 0:
+            continue
+        for ch, sign in ((1, (-1.0) ** xx), (2, (-1.0) ** yy)):
+            sm = sign * m
+            out[k, :, :, ch] -= ((sm * y[k, :, :, ch]).sum() / nf) * sm
+    return out
+
+
+def output_stage(y, fluid):
+    return unstagger(smooth(y, fluid), fluid)
+
+
+def output_stage_backward(g, fluid):
+    return smooth(unstagger(g, fluid), fluid)
+
+
 def layer_shapes(channels, cin=4, cout=3):
     """(cin, cout) of the convolutions, in the order of the forward pass."""
     L = len(channels)
@@ -119,11 +177,23 @@ def init_params(channels, seed, cin=4, cout=3):
 
 
 class WarmNet:
-    def __init__(self, channels, params, bf16_storage=False):
+    def __init__(self, channels, params, bf16_storage=False, sum_noise=None):
+        """sum_noise: None, or a seed.  With a seed, every convolution sum
+        (forward and input gradient) is multiplied by 1 + 2^-24 sqrt(K) xi,
+        xi standard normal, K the number of terms: the size of the error of
+        an FP32 accumulation.  Running the reference with and without it
+        shows how far the rounding of stored bfloat16 values alone carries
+        such an error through the network."""
         self.channels = list(channels)
         self.L = len(channels)
         self.rnd = bf16 if bf16_storage else (lambda v: v)
         self.params = [(self.rnd(w), b.copy()) for w, b in params]
+        self.noise = None if sum_noise is None else np.random.default_rng(sum_noise)
+
+    def _sum_error(self, v, terms):
+        if self.noise is None:
+            return v
+        return v * (1.0 + 2.0 ** -24 * np.sqrt(terms) * self.noise.standard_normal(v.shape))
 
     def forward(self, x):
         """Returns the output and the tape of stored activations."""
@@ -135,13 +205,14 @@ class WarmNet:
         def conv(v, relu):
             nonlocal k
             w, b = P[k]
-            pre = conv3x3(v, w, b)
+            pre = self._sum_error(conv3x3(v, w, b), 9 * v.shape[3])
             k += 1
             out = r(np.maximum(pre, 0.0) if relu else pre)
             tape.append(("conv", v, k - 1, relu, out))
             return out
 
         x = r(x)
+        fluid = fluid_of_input(x)
         skips = []
         for l in range(self.L):
             x = conv(x, True)
@@ -158,7 +229,8 @@ class WarmNet:
             tape.append(("skip", l))
             x = conv(x, True)
         y = conv(x, False)
-        return y, tape
+        tape.append(("out", fluid))
+        return output_stage(y, fluid), tape
 
     def loss(self, y, target, fluid):
         m = fluid[..., None].astype(np.float64)
@@ -179,15 +251,17 @@ class WarmNet:
         for item in tape:
             if item[0] == "pool":
                 pool_level += 1
-        g = r(gy)
+        g = gy
         for item in reversed(tape):
-            if item[0] == "conv":
+            if item[0] == "out":
+                g = r(output_stage_backward(g, item[1]))
+            elif item[0] == "conv":
                 _, xin, k, relu, out = item
                 if relu:
                     g = g * (out > 0.0)
                 gx, gw, gb = conv3x3_backward(xin, self.params[k][0], g)
                 grads[k] = (gw, gb)
-                g = r(gx)
+                g = r(self._sum_error(gx, 9 * g.shape[3]))
             elif item[0] == "skip":
                 skip_grads[item[1]] = g
             elif item[0] == "up":

@@ -764,11 +764,15 @@ lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]) {
     if (!h->uprev) CK(h, lbm::dev_alloc(&h->uprev, 2 * (size_t)h->N * sizeof(double)), "cudaMalloc(residual)");
     const AuxParams a = aux(h);
     const int have = h->have_prev && h->steps > h->prev_step;
+    // the state one step earlier is the other buffer once a step has run
+    const void* prev = h->steps >= 1 ? h->f[h->cur ^ 1] : nullptr;
     cudaError_t e = h->p.precision == 64
-                        ? lbm::launch_diag<double>((const double*)h->f[h->cur], a, h->uprev, have,
-                                                   h->part, h->diag_blocks, h->stream)
-                        : lbm::launch_diag<float>((const float*)h->f[h->cur], a, h->uprev, have,
-                                                  h->part, h->diag_blocks, h->stream);
+                        ? lbm::launch_diag<double>((const double*)h->f[h->cur], (const double*)prev,
+                                                   a, h->uprev, have, h->part, h->diag_blocks,
+                                                   h->stream)
+                        : lbm::launch_diag<float>((const float*)h->f[h->cur], (const float*)prev, a,
+                                                  h->uprev, have, h->part, h->diag_blocks,
+                                                  h->stream);
     CK(h, e, "diagnostics kernels");
     DiagPartial r;
     CK(h, cudaMemcpyAsync(&r, h->part + h->diag_blocks, sizeof(r), cudaMemcpyDeviceToHost, h->stream),
@@ -790,6 +794,7 @@ lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]) {
                  : -1.0;
     out[5] = (double)r.nonfinite;
     out[6] = (double)h->steps;
+    out[7] = (prev && r.ures > 0.0) ? std::sqrt(r.sres) / std::sqrt(r.ures) : -1.0;
     h->have_prev = 1;
     h->prev_step = h->steps;
     if (r.nonfinite > 0) {
@@ -906,11 +911,12 @@ extern "C" lbm_status lbm_diagnostics_noalloc(lbm_handle* h, double out[LBM_DIAG
     // block writes its own partial and the final sum overwrites its slot).
     const int have = d.owner == h->serial && h->steps > d.step;
     const AuxParams a = aux(h);
+    const void* prev = h->steps >= 1 ? h->f[h->cur ^ 1] : nullptr;
     cudaError_t e = h->p.precision == 64
-                        ? lbm::launch_diag<double>((const double*)h->f[h->cur], a, uref, have,
-                                                   part, h->diag_blocks, h->stream)
-                        : lbm::launch_diag<float>((const float*)h->f[h->cur], a, uref, have,
-                                                  part, h->diag_blocks, h->stream);
+                        ? lbm::launch_diag<double>((const double*)h->f[h->cur], (const double*)prev,
+                                                   a, uref, have, part, h->diag_blocks, h->stream)
+                        : lbm::launch_diag<float>((const float*)h->f[h->cur], (const float*)prev, a,
+                                                  uref, have, part, h->diag_blocks, h->stream);
     CK(h, e, "diagnostics kernels");
     DiagPartial r;
     CK(h, cudaMemcpyAsync(&r, part + h->diag_blocks, sizeof(r), cudaMemcpyDeviceToHost,
@@ -934,6 +940,7 @@ extern "C" lbm_status lbm_diagnostics_noalloc(lbm_handle* h, double out[LBM_DIAG
                  : -1.0;
     out[5] = (double)r.nonfinite;
     out[6] = (double)h->steps;
+    out[7] = (prev && r.ures > 0.0) ? std::sqrt(r.sres) / std::sqrt(r.ures) : -1.0;
     d.owner = h->serial;
     d.step = h->steps;
     if (r.nonfinite > 0) {
@@ -991,6 +998,8 @@ struct lbm_batch {
     bool has_scheme[2] = {false, false};
     int n_active = 0, total_chunks = 0;
     bool list_dirty = true;
+    int* d_two = nullptr;          // per lattice: its other buffer holds the previous step
+    std::vector<int> h_two;
     ResPartial* d_part = nullptr;  // per reduction block
     ResPartial* d_res = nullptr;   // per lattice
     std::vector<ResPartial> h_res;
@@ -1279,6 +1288,8 @@ lbm_status lbm_batch_create(const lbm_params* params, int count,
     for (int k = 0; k < count; ++k) b->has_scheme[params[k].scheme == 1 ? 1 : 0] = true;
     BCKC(lbm::dev_alloc(&b->d_part, sizeof(ResPartial) * (size_t)chunks), "cudaMalloc(residual sums)");
     BCKC(lbm::dev_alloc(&b->d_res, sizeof(ResPartial) * (size_t)count), "cudaMalloc(residual sums)");
+    BCKC(lbm::dev_alloc(&b->d_two, sizeof(int) * (size_t)count), "cudaMalloc(residual flags)");
+    b->h_two.assign(count, 0);
     b->diag_blocks = 2 * b->sms;
     BCKC(lbm::dev_alloc(&b->d_diag, sizeof(DiagPartial) * (b->diag_blocks + 1)),
          "cudaMalloc(diagnostics)");
@@ -1330,6 +1341,7 @@ void lbm_batch_destroy(lbm_batch* b) {
     cudaFree(b->d_list);
     cudaFree(b->d_part);
     cudaFree(b->d_res);
+    cudaFree(b->d_two);
     cudaFree(b->d_diag);
     cudaFree(b->status);
     cudaFree(b->stage);
@@ -1460,10 +1472,16 @@ lbm_status lbm_batch_residuals(lbm_batch* b, double* res) {
     const int C = b->count;
     int kstatus = 0;
     if (b->n_active > 0) {
+        // a lattice stepped since its last init holds its previous state in
+        // its other buffer: its residual is then on the two-step mean
+        for (int k = 0; k < C; ++k) b->h_two[k] = b->steps[k] >= 1;
+        BCK(b, cudaMemcpyAsync(b->d_two, b->h_two.data(), sizeof(int) * C, cudaMemcpyHostToDevice,
+                               b->stream),
+            "cudaMemcpyAsync(residual flags)");
         const int* Lr = b->d_list + list_at(b, 2);
-        BCK(b, lbm::launch_batch_residual(b->d_lat, b->d_aux, Lr, Lr + C, Lr + 2 * C, b->parity,
-                                          b->d_part, b->d_res, b->n_active, b->total_chunks,
-                                          b->stream),
+        BCK(b, lbm::launch_batch_residual(b->d_lat, b->d_aux, Lr, Lr + C, Lr + 2 * C, b->d_two,
+                                          b->parity, b->d_part, b->d_res, b->n_active,
+                                          b->total_chunks, b->stream),
             "batch residual kernels");
         BCK(b, cudaMemcpyAsync(b->h_res.data(), b->d_res, sizeof(ResPartial) * C,
                                cudaMemcpyDeviceToHost, b->stream),

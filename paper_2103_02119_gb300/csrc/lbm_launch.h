@@ -16,7 +16,9 @@ constexpr int kMassLimbs = 8;
 constexpr int kMassShift = 144;
 // Per-block partial results of the diagnostics reduction.
 struct DiagPartial {
-    double mx, my, en, dres, ures;  // sum rho ux, rho uy, rho|u|^2/2, |du|^2, |u|^2
+    // sum rho ux, rho uy, rho |u|^2 / 2 over the current state; |ubar - uref|^2,
+    // |ubar|^2 of the two-step mean ubar = (u(n) + u(n-1)) / 2; |u(n) - u(n-1)|^2
+    double mx, my, en, dres, ures, sres;
     long long nonfinite;
     long long limb[kMassLimbs];
 };
@@ -70,14 +72,16 @@ struct ResPartial {
     double dres, ures;
     long long nonfinite;
 };
-// Residual sums of every active lattice from its FP32 state lat[k].f[parity]:
-// counts = {active lattices, total reduction blocks}, rbegin[j] = first
-// block of active[j]; writes out[active[j]] and overwrites uprev.  The host
-// passes the same two counts as nactive / nblocks (launch sizes).
+// Residual sums of every active lattice from its FP32 state lat[k].f[parity]
+// and, where two[k] != 0, its state one step earlier lat[k].f[parity ^ 1]
+// (the residual is then on the two-step mean velocity): counts = {active
+// lattices, total reduction blocks}, rbegin[j] = first block of active[j];
+// writes out[active[j]] and overwrites uprev.  The host passes the same two
+// counts as nactive / nblocks (launch sizes).
 cudaError_t launch_batch_residual(const BatchLattice<float>* lat, const BatchAux* aux,
                                   const int* active, const int* rbegin, const int* counts,
-                                  int parity, ResPartial* part, ResPartial* out, int nactive,
-                                  int nblocks, cudaStream_t s);
+                                  const int* two, int parity, ResPartial* part,
+                                  ResPartial* out, int nactive, int nblocks, cudaStream_t s);
 
 // f = f^eq(rho, u) (device inputs, nullable), written in pull-scheme form.
 template <typename T>
@@ -102,10 +106,11 @@ cudaError_t launch_stress(const T* f, const AuxParams& p, const double* rho, dou
                           double* dyuy, double* sxy, double* txx, double* tyy, double* txy,
                           cudaStream_t s);
 // diagnostics: per-block partials into `part` (nblocks entries) then a final
-// reduction into part[nblocks]; uprev (2*nx*ny doubles) is read (if
-// have_prev) and overwritten with the current velocity.
+// reduction into part[nblocks]; fprev: the state one step earlier (nullable:
+// the residual then uses u(n) alone); uprev (2*nx*ny doubles) is read (if
+// have_prev) and overwritten with the two-step mean velocity.
 template <typename T>
-cudaError_t launch_diag(const T* f, const AuxParams& p, double* uprev, int have_prev,
-                        DiagPartial* part, int nblocks, cudaStream_t s);
+cudaError_t launch_diag(const T* f, const T* fprev, const AuxParams& p, double* uprev,
+                        int have_prev, DiagPartial* part, int nblocks, cudaStream_t s);
 
 }  // namespace lbm

@@ -364,17 +364,6 @@ __global__ void pack_input_kernel(const float* x, bf16* out, long long pixels, i
     }
 }
 
-__global__ void unpack_output_kernel(const bf16* y, float* out, long long pixels, int cout,
-                                     int cp) {
-    const long long total = pixels * cout;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int ch = (int)(i % cout);
-        const long long p = i / cout;
-        out[i] = __bfloat162float(y[p * cp + ch]);
-    }
-}
-
 template <typename V>
 __device__ __forceinline__ V block_sum(V v) {
     __shared__ V sh[kThreads / 32];
@@ -390,24 +379,123 @@ __device__ __forceinline__ V block_sum(V v) {
     return s;  // valid in thread 0
 }
 
-// Masked squared error: per-block partial sums (FP64) and the output gradient
-// 2 (y - t) fluid / cnt, stored BF16 in the padded layout.
-__global__ void __launch_bounds__(kThreads) loss_kernel(const bf16* y, const float* t,
-                                                        const uint8_t* fluid, bf16* gy,
+// ---- the fixed output stage: masked smoothing and the staggered projection ----
+//
+// smooth:    out(p) = fl(p) sum_{dy,dx} w(dy) w(dx) fl(q) in(q), q = p + (dy, dx)
+//            inside the grid, w = (1/4, 1/2, 1/4); fl from input channel 0
+// unstagger: channel 1 minus its projection on (-1)^x, channel 2 minus its
+//            projection on (-1)^y, over the fluid cells of each instance
+// Both are self-adjoint: the backward pass applies unstagger, then smooth.
+
+__device__ __forceinline__ bool fluid_at(const bf16* xin, int xcp, long long p) {
+    return __bfloat162float(xin[p * xcp]) < 0.5f;
+}
+
+// in: bf16 [P][icp] or float [P][3]; out: float [P][3] or bf16 [P][ocp] (the
+// channels past 3 zeroed)
+template <bool IN_BF16, bool OUT_BF16>
+__global__ void out_smooth_kernel(const void* in, int icp, const bf16* xin, int xcp, void* out,
+                                  int ocp, int n, int h, int w) {
+    const long long P = (long long)n * h * w;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(p % w);
+        const long long r = p / w;
+        const int y = (int)(r % h);
+        const long long base = r / h * h;
+        float acc[3] = {0.0f, 0.0f, 0.0f};
+        if (fluid_at(xin, xcp, p)) {
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int yy = y + dy;
+                if (yy < 0 || yy >= h) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int xx = x + dx;
+                    if (xx < 0 || xx >= w) continue;
+                    const long long q = (base + yy) * w + xx;
+                    if (!fluid_at(xin, xcp, q)) continue;
+                    const float wt = (dy == 0 ? 0.5f : 0.25f) * (dx == 0 ? 0.5f : 0.25f);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float v = IN_BF16
+                                            ? __bfloat162float(static_cast<const bf16*>(in)[q * icp + c])
+                                            : static_cast<const float*>(in)[q * 3 + c];
+                        acc[c] = fmaf(wt, v, acc[c]);
+                    }
+                }
+            }
+        }
+        if (OUT_BF16) {
+            bf16* o = static_cast<bf16*>(out) + p * ocp;
+            for (int c = 0; c < ocp; ++c) o[c] = __float2bfloat16_rn(c < 3 ? acc[c] : 0.0f);
+        } else {
+            float* o = static_cast<float*>(out) + p * 3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[c] = acc[c];
+        }
+    }
+}
+
+// Block k: sums over the fluid cells of instance k of (-1)^x v1, (-1)^y v2 and
+// the cell count, in a fixed order.
+__global__ void __launch_bounds__(kThreads) stagger_sum_kernel(const float* v, const bf16* xin,
+                                                               int xcp, double* sums, int h,
+                                                               int w) {
+    const long long hw = (long long)h * w, p0 = (long long)blockIdx.x * hw;
+    double s1 = 0.0, s2 = 0.0, nf = 0.0;
+    for (long long i = threadIdx.x; i < hw; i += blockDim.x) {
+        const long long p = p0 + i;
+        if (!fluid_at(xin, xcp, p)) continue;
+        const int x = (int)(i % w), y = (int)(i / w);
+        s1 += (x & 1) ? -(double)v[p * 3 + 1] : (double)v[p * 3 + 1];
+        s2 += (y & 1) ? -(double)v[p * 3 + 2] : (double)v[p * 3 + 2];
+        nf += 1.0;
+    }
+    s1 = block_sum(s1);
+    s2 = block_sum(s2);
+    nf = block_sum(nf);
+    if (threadIdx.x == 0) {
+        sums[3 * blockIdx.x] = s1;
+        sums[3 * blockIdx.x + 1] = s2;
+        sums[3 * blockIdx.x + 2] = nf;
+    }
+}
+
+__global__ void stagger_apply_kernel(const float* v, const bf16* xin, int xcp,
+                                     const double* sums, float* out, long long P, int h, int w) {
+    const long long hw = (long long)h * w;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long k = p / hw, i = p - k * hw;
+        const int x = (int)(i % w), y = (int)(i / w);
+        float o1 = v[p * 3 + 1], o2 = v[p * 3 + 2];
+        const double nf = sums[3 * k + 2];
+        if (nf > 0.0 && fluid_at(xin, xcp, p)) {
+            const float c1 = (float)(sums[3 * k] / nf), c2 = (float)(sums[3 * k + 1] / nf);
+            o1 -= (x & 1) ? -c1 : c1;
+            o2 -= (y & 1) ? -c2 : c2;
+        }
+        out[p * 3] = v[p * 3];
+        out[p * 3 + 1] = o1;
+        out[p * 3 + 2] = o2;
+    }
+}
+
+// Masked squared error of the network's output y (FP32 [P][3], after the
+// output stage): per-block partial sums (FP64) and the output gradient
+// 2 (y - t) fluid / cnt (FP32 [P][3]).
+__global__ void __launch_bounds__(kThreads) loss_kernel(const float* y, const float* t,
+                                                        const uint8_t* fluid, float* gy,
                                                         double* part, long long pixels,
-                                                        int cout, int cp, float inv_cnt) {
+                                                        float inv_cnt) {
     double s = 0.0;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < pixels;
          p += (long long)gridDim.x * blockDim.x) {
         const float m = fluid[p] ? 1.0f : 0.0f;
-        for (int c = 0; c < cp; ++c) {
-            float gv = 0.0f;
-            if (c < cout) {
-                const float d = (__bfloat162float(y[p * cp + c]) - t[p * cout + c]) * m;
-                s += (double)d * (double)d;
-                gv = 2.0f * d * inv_cnt;
-            }
-            gy[p * cp + c] = __float2bfloat16_rn(gv);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float d = (y[p * 3 + c] - t[p * 3 + c]) * m;
+            s += (double)d * (double)d;
+            gy[p * 3 + c] = 2.0f * d * inv_cnt;
         }
     }
     const double b = block_sum(s);
@@ -518,7 +606,10 @@ struct lbm_nn {
     float* xin = nullptr;      // staging of host inputs (float)
     float* tgt = nullptr;
     uint8_t* fl = nullptr;
-    float* yout = nullptr;
+    float* yout = nullptr;     // the network's output after the output stage [P][3]
+    float* gout = nullptr;     // the loss gradient of yout [P][3]
+    float* tmp3 = nullptr;     // the output stage's intermediate [P][3]
+    double* ssum = nullptr;    // per instance: the staggered sums and fluid count
     long long adam_t = 0;
     int64_t launches = 0;
     char err[512] = {0};
@@ -639,6 +730,19 @@ lbm_status upload_inputs(lbm_nn* nn, const float* x, const float* tgt, const uin
     return LBM_OK;
 }
 
+// out = the staggered projection of v (FP32 [P][3] each), per instance.
+lbm_status unstagger(lbm_nn* nn, int n, const float* v, float* out) {
+    const lbm_nn::Tensor& X = nn->t[nn->x_id];
+    const long long P = pixels(nn, nn->x_id, n);
+    stagger_sum_kernel<<<n, kThreads, 0, nn->stream>>>(v, X.v, X.cp, nn->ssum, X.h, X.w);
+    NCK(nn, cudaGetLastError(), "staggered sums");
+    stagger_apply_kernel<<<grid_of(P), kThreads, 0, nn->stream>>>(v, X.v, X.cp, nn->ssum, out, P,
+                                                                  X.h, X.w);
+    NCK(nn, cudaGetLastError(), "staggered projection");
+    nn->launches += 3;  // with the smoothing launched beside it
+    return LBM_OK;
+}
+
 lbm_status forward(lbm_nn* nn, int n) {
     const cudaStream_t s = nn->stream;
     for (const auto& op : nn->ops) {
@@ -675,7 +779,14 @@ lbm_status forward(lbm_nn* nn, int n) {
         NCK(nn, e, "forward kernels");
         ++nn->launches;
     }
-    return LBM_OK;
+    // the fixed output stage: yout = unstagger(smooth(y))
+    const lbm_nn::Tensor& X = nn->t[nn->x_id];
+    const lbm_nn::Tensor& Y = nn->t[nn->y_id];
+    const long long P = pixels(nn, nn->y_id, n);
+    out_smooth_kernel<true, false><<<grid_of(P), kThreads, 0, s>>>(Y.v, Y.cp, X.v, X.cp, nn->tmp3,
+                                                                   3, n, Y.h, Y.w);
+    NCK(nn, cudaGetLastError(), "output smoothing");
+    return unstagger(nn, n, nn->tmp3, nn->yout);
 }
 
 // Loss of the batch (synchronous) and, through the backward pass, the
@@ -692,14 +803,21 @@ lbm_status backward(lbm_nn* nn, int n, float* loss) {
     const float inv_cnt = nf > 0 ? (float)(1.0 / (3.0 * (double)nf)) : 0.0f;
     std::vector<bf16*> G(nn->t.size());
     for (size_t i = 0; i < nn->t.size(); ++i) G[i] = nn->t[i].g;
+    const lbm_nn::Tensor& X = nn->t[nn->x_id];
     const lbm_nn::Tensor& Y = nn->t[nn->y_id];
     const int lb = grid_of(P) < 1024 ? grid_of(P) : 1024;
-    loss_kernel<<<lb, kThreads, 0, s>>>(Y.v, nn->tgt, nn->fl, G[nn->y_id], nn->dpart, P, 3, Y.cp,
+    loss_kernel<<<lb, kThreads, 0, s>>>(nn->yout, nn->tgt, nn->fl, nn->gout, nn->dpart, P,
                                         inv_cnt);
     NCK(nn, cudaGetLastError(), "loss kernel");
     sum_kernel<<<1, kThreads, 0, s>>>(nn->dpart, lb, nn->dpart + 1024);
     NCK(nn, cudaGetLastError(), "loss sum");
     nn->launches += 2;
+    // the output stage backward: unstagger, then smooth into the gradient of
+    // the last convolution's output (BF16, padded channels zeroed)
+    if (lbm_status st = unstagger(nn, n, nn->gout, nn->tmp3); st != LBM_OK) return st;
+    out_smooth_kernel<false, true><<<grid_of(P), kThreads, 0, s>>>(nn->tmp3, 3, X.v, X.cp,
+                                                                   G[nn->y_id], Y.cp, n, Y.h, Y.w);
+    NCK(nn, cudaGetLastError(), "output smoothing (backward)");
     std::vector<char> pool_seen(nn->t.size(), 0);
     for (int i = (int)nn->ops.size() - 1; i >= 0; --i) {
         const lbm_nn::Op& op = nn->ops[i];
@@ -892,6 +1010,9 @@ lbm_status lbm_nn_create(int levels, const int* channels, int max_batch, int hei
     NCKC(lbm::dev_alloc(&nn->tgt, Pmax * 3 * sizeof(float)), "cudaMalloc(targets)");
     NCKC(lbm::dev_alloc(&nn->fl, Pmax), "cudaMalloc(fluid)");
     NCKC(lbm::dev_alloc(&nn->yout, Pmax * 3 * sizeof(float)), "cudaMalloc(outputs)");
+    NCKC(lbm::dev_alloc(&nn->gout, Pmax * 3 * sizeof(float)), "cudaMalloc(output gradient)");
+    NCKC(lbm::dev_alloc(&nn->tmp3, Pmax * 3 * sizeof(float)), "cudaMalloc(output stage)");
+    NCKC(lbm::dev_alloc(&nn->ssum, (size_t)nn->nb * 3 * sizeof(double)), "cudaMalloc(output sums)");
 #undef NCKC
     // He-normal initial weights (host generator), zero biases
     std::vector<float> params(lbm_nn_param_count(nn));
@@ -921,6 +1042,9 @@ void lbm_nn_destroy(lbm_nn* nn) {
     cudaFree(nn->tgt);
     cudaFree(nn->fl);
     cudaFree(nn->yout);
+    cudaFree(nn->gout);
+    cudaFree(nn->tmp3);
+    cudaFree(nn->ssum);
     delete nn;
 }
 
@@ -1005,10 +1129,6 @@ lbm_status lbm_nn_forward(lbm_nn* nn, const float* x, int n, float* y) {
     if (s == LBM_OK) s = forward(nn, n);
     if (s != LBM_OK) return s;
     const long long P = (long long)n * nn->H * nn->W;
-    const lbm_nn::Tensor& Y = nn->t[nn->y_id];
-    unpack_output_kernel<<<grid_of(P * 3), kThreads, 0, nn->stream>>>(Y.v, nn->yout, P, 3, Y.cp);
-    NCK(nn, cudaGetLastError(), "output unpacking");
-    ++nn->launches;
     NCK(nn, cudaMemcpyAsync(y, nn->yout, P * 3 * sizeof(float), cudaMemcpyDeviceToHost,
                             nn->stream),
         "cudaMemcpyAsync(D2H)");

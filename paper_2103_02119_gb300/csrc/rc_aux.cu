@@ -383,6 +383,7 @@ __device__ void block_reduce(DiagPartial& d, DiagPartial* out) {
     d.en = warp_sum(d.en);
     d.dres = warp_sum(d.dres);
     d.ures = warp_sum(d.ures);
+    d.sres = warp_sum(d.sres);
     d.nonfinite = warp_sum(d.nonfinite);
 #pragma unroll
     for (int k = 0; k < kMassLimbs; ++k) d.limb[k] = warp_sum(d.limb[k]);
@@ -396,6 +397,7 @@ __device__ void block_reduce(DiagPartial& d, DiagPartial* out) {
             s.en += sh[i].en;
             s.dres += sh[i].dres;
             s.ures += sh[i].ures;
+            s.sres += sh[i].sres;
             s.nonfinite += sh[i].nonfinite;
             for (int k = 0; k < kMassLimbs; ++k) s.limb[k] += sh[i].limb[k];
         }
@@ -403,10 +405,17 @@ __device__ void block_reduce(DiagPartial& d, DiagPartial* out) {
     }
 }
 
+// The steady residual is taken on the two-step mean velocity
+// ubar(n) = (u(n) + u(n-1)) / 2 when the state one step earlier is at hand
+// (fprev, the other buffer): the scheme carries exact invariants, the
+// staggered momenta sum (-1)^(x+n) rho ux and sum (-1)^(y+n) rho uy, whose
+// motion alternates sign every step; a residual between two states an even
+// number of steps apart never sees it, and the mean cancels it.  The
+// step-to-step change |u(n) - u(n-1)|^2 is summed beside it.
 template <typename T, bool MASK>
 __global__ void __launch_bounds__(kThreads)
-diag_kernel(const T* __restrict__ f, const AuxParams p, double* __restrict__ uprev,
-            int have_prev, DiagPartial* part) {
+diag_kernel(const T* __restrict__ f, const T* __restrict__ fprev, const AuxParams p,
+            double* __restrict__ uprev, int have_prev, DiagPartial* part) {
     const long long N = (long long)p.nx * p.ny;
     DiagPartial d = {};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
@@ -428,13 +437,24 @@ diag_kernel(const T* __restrict__ f, const AuxParams p, double* __restrict__ upr
         d.mx += rho * ux;
         d.my += rho * uy;
         d.en += 0.5 * rho * (ux * ux + uy * uy);
-        d.ures += ux * ux + uy * uy;
+        double mx = ux, my = uy;
+        if (fprev) {
+            T q[9];
+            pull(fprev, p, x, y, sb, q);
+            double r1, ux1, uy1;
+            macro(p, q, r1, ux1, uy1);
+            const double sx = ux - ux1, sy = uy - uy1;
+            d.sres += sx * sx + sy * sy;
+            mx = 0.5 * (ux + ux1);
+            my = 0.5 * (uy + uy1);
+        }
+        d.ures += mx * mx + my * my;
         if (have_prev) {
-            const double du = ux - uprev[c], dv = uy - uprev[N + c];
+            const double du = mx - uprev[c], dv = my - uprev[N + c];
             d.dres += du * du + dv * dv;
         }
-        uprev[c] = ux;
-        uprev[N + c] = uy;
+        uprev[c] = mx;
+        uprev[N + c] = my;
     }
     block_reduce(d, part + blockIdx.x);
 }
@@ -448,6 +468,7 @@ __global__ void __launch_bounds__(kThreads) diag_final(DiagPartial* part, int n)
         d.en += q.en;
         d.dres += q.dres;
         d.ures += q.ures;
+        d.sres += q.sres;
         d.nonfinite += q.nonfinite;
         for (int k = 0; k < kMassLimbs; ++k) d.limb[k] += q.limb[k];
     }
@@ -479,7 +500,8 @@ __device__ void res_block_reduce(ResPartial& d, ResPartial* out) {
 __global__ void __launch_bounds__(kThreads)
 batch_res_kernel(const BatchLattice<float>* __restrict__ lat, const BatchAux* __restrict__ aux,
                  const int* __restrict__ active, const int* __restrict__ rbegin,
-                 const int* __restrict__ counts, int parity, ResPartial* part) {
+                 const int* __restrict__ counts, const int* __restrict__ two, int parity,
+                 ResPartial* part) {
     const int n = counts[0];
     const int w = blockIdx.x;
     if (w >= counts[1]) return;
@@ -493,6 +515,7 @@ batch_res_kernel(const BatchLattice<float>* __restrict__ lat, const BatchAux* __
     const BatchAux& B = aux[k];
     const AuxParams& p = B.a;
     const float* f = lat[k].f[parity];
+    const float* fp = two[k] ? lat[k].f[parity ^ 1] : nullptr;  // one step earlier
     const int chunk = w - rbegin[lo];
     const long long N = (long long)p.nx * p.ny;
     double* __restrict__ up = B.uprev;
@@ -510,11 +533,20 @@ batch_res_kernel(const BatchLattice<float>* __restrict__ lat, const BatchAux* __
             d.nonfinite += 1;
             continue;
         }
-        const double du = ux - up[c], dv = uy - up[N + c];
+        double mx = ux, my = uy;  // the two-step mean velocity, as in diag_kernel
+        if (fp) {
+            float q[9];
+            pull(fp, p, x, y, sb, q);
+            double r1, ux1, uy1;
+            macro(p, q, r1, ux1, uy1);
+            mx = 0.5 * (ux + ux1);
+            my = 0.5 * (uy + uy1);
+        }
+        const double du = mx - up[c], dv = my - up[N + c];
         d.dres += du * du + dv * dv;
-        d.ures += ux * ux + uy * uy;
-        up[c] = ux;
-        up[N + c] = uy;
+        d.ures += mx * mx + my * my;
+        up[c] = mx;
+        up[N + c] = my;
     }
     res_block_reduce(d, part + B.pbegin + chunk);
 }
@@ -611,10 +643,12 @@ cudaError_t launch_stress(const T* f, const AuxParams& p, const double* rho, dou
 }
 
 template <typename T>
-cudaError_t launch_diag(const T* f, const AuxParams& p, double* uprev, int have_prev,
-                        DiagPartial* part, int nblocks, cudaStream_t s) {
-    if (p.lmask) diag_kernel<T, true><<<nblocks, kThreads, 0, s>>>(f, p, uprev, have_prev, part);
-    else diag_kernel<T, false><<<nblocks, kThreads, 0, s>>>(f, p, uprev, have_prev, part);
+cudaError_t launch_diag(const T* f, const T* fprev, const AuxParams& p, double* uprev,
+                        int have_prev, DiagPartial* part, int nblocks, cudaStream_t s) {
+    if (p.lmask)
+        diag_kernel<T, true><<<nblocks, kThreads, 0, s>>>(f, fprev, p, uprev, have_prev, part);
+    else
+        diag_kernel<T, false><<<nblocks, kThreads, 0, s>>>(f, fprev, p, uprev, have_prev, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     diag_final<<<1, kThreads, 0, s>>>(part, nblocks);
@@ -623,10 +657,11 @@ cudaError_t launch_diag(const T* f, const AuxParams& p, double* uprev, int have_
 
 cudaError_t launch_batch_residual(const BatchLattice<float>* lat, const BatchAux* aux,
                                   const int* active, const int* rbegin, const int* counts,
-                                  int parity, ResPartial* part, ResPartial* out, int nactive,
-                                  int nblocks, cudaStream_t s) {
+                                  const int* two, int parity, ResPartial* part,
+                                  ResPartial* out, int nactive, int nblocks, cudaStream_t s) {
     if (nactive <= 0 || nblocks <= 0) return cudaSuccess;
-    batch_res_kernel<<<nblocks, kThreads, 0, s>>>(lat, aux, active, rbegin, counts, parity, part);
+    batch_res_kernel<<<nblocks, kThreads, 0, s>>>(lat, aux, active, rbegin, counts, two, parity,
+                                                  part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     batch_res_final<<<nactive, kThreads, 0, s>>>(aux, active, counts, part, out);
@@ -645,7 +680,7 @@ cudaError_t launch_batch_residual(const BatchLattice<float>* lat, const BatchAux
     template cudaError_t launch_stress<T>(const T*, const AuxParams&, const double*,  \
                                           double*, double*, double*, double*, double*, \
                                           double*, cudaStream_t);                     \
-    template cudaError_t launch_diag<T>(const T*, const AuxParams&, double*, int,     \
+    template cudaError_t launch_diag<T>(const T*, const T*, const AuxParams&, double*, int, \
                                         DiagPartial*, int, cudaStream_t);
 LBM_AUX_INST(float)
 LBM_AUX_INST(double)

@@ -5,12 +5,6 @@
 
 namespace lbm {
 
-// Resident 128-thread blocks per SM the batch kernel is bounded for.
-#ifndef LBM_BATCH_BLOCKS
-#define LBM_BATCH_BLOCKS 4
-#endif
-constexpr int kBatchBlocks128 = LBM_BATCH_BLOCKS;
-
 // Persistent kernel over many lattices of one scheme (SCH: 0 RC-LBM or no
 // collision, 1 RNR-LBM): block b takes work items b,
 // b + gridDim.x, ... of a device work list; item w belongs to the active
@@ -22,7 +16,7 @@ constexpr int kBatchBlocks128 = LBM_BATCH_BLOCKS;
 // step's constant-bank operands; at 96 registers the kernel spills, and
 // unbounded (168 registers, three blocks) it ran 18 % slower.
 template <typename T, int BXT, int SCH>
-__global__ void __launch_bounds__(BXT, kBatchBlocks128 * 128 / BXT)
+__global__ void __launch_bounds__(BXT, 512 / BXT)
 rc_batch_kernel(const BatchLattice<T>* __restrict__ lat, const int* __restrict__ active,
                 const int* __restrict__ begin, const int* __restrict__ counts, int parity) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -47,8 +41,8 @@ rc_batch_kernel(const BatchLattice<T>* __restrict__ lat, const int* __restrict__
         const T* fin = L->f[parity];
         T* fout = L->f[parity ^ 1];
         // lattices of a batch stay below 2^31 elements (checked on the host)
-        if (!step_block<T, true, BXT, int, SCH, const KParams<T>&, true>(
-                fin, fout, kp, L->nbands, local % nseg, local / nseg, smem))
+        if (!step_block<T, true, BXT, int, SCH, const KParams<T>&>(fin, fout, kp, L->nbands,
+                                                              local % nseg, local / nseg, smem))
             return;
     }
 }

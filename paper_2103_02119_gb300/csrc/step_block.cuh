@@ -154,37 +154,12 @@ __device__ __forceinline__ void mbar_inval(unsigned bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// The collision's constants, read afresh at each use from a parameter block
-// in shared memory (a lattice of a batch): one broadcast load per constant
-// (the low half of its lane pair, duplicated), which the compiler may not
-// hoist out of the row loop, so that the constants occupy registers only
-// during the collision, as the constant-bank operands of a single-lattice
-// kernel do.
-__device__ __forceinline__ CollConst<float> fresh_consts(const CollConst<float>& src) {
-    constexpr int n = sizeof(CollConst<float>) / sizeof(float2);
-    static_assert(sizeof(CollConst<float>) % sizeof(float2) == 0, "constants are lane pairs");
-    const volatile float* s = reinterpret_cast<const volatile float*>(&src);
-    CollConst<float> c;
-    float2* d = reinterpret_cast<float2*>(&c);
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-        const float v = s[2 * i];
-        d[i] = make_float2(v, v);
-    }
-    return c;
-}
-__device__ __forceinline__ CollConst<double> fresh_consts(const CollConst<double>& src) {
-    return src;
-}
-
 // One block's work: segment `seg` of columns and row band `band` (of nbands)
 // of one lattice, from fin to fout.  smem: step_smem_bytes<T, BXT>() bytes.
 // Returns false when a wait ran out (the block must stop).
 // PT: KParams<T> or const KParams<T>& (a kernel parameter, or the copy in
-// shared memory of a lattice of a batch).  SMEMP: the parameters are in
-// shared memory (the collision's constants are then re-read at each use).
-template <typename T, bool MASK, int BXT, typename I, int SCH, typename PT = KParams<T>,
-          bool SMEMP = false>
+// shared memory of a lattice of a batch).
+template <typename T, bool MASK, int BXT, typename I, int SCH, typename PT = KParams<T>>
 __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restrict__ fout,
                                            const PT p, int nbands, int seg, int band,
                                            unsigned char* smem) {
@@ -199,10 +174,10 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
 
     const int tx = threadIdx.x;
     const int lane = tx & 31;
-    // the warp that issues the copies: warp 1 of four, not warp 0, which
-    // adds the halo densities (the per-row barrier waits on the slowest
-    // warp)
-    constexpr int kIssueWarp = BXT >= 128 ? 1 : 0;
+    // the warp that issues the copies: warp 1, not warp 0, which adds the
+    // halo densities (the per-row barrier waits on the slowest warp); a
+    // one-warp block does both
+    constexpr int kIssueWarp = BXT >= 64 ? 1 : 0;
     const int x0 = seg * W;
     const int nseg = min(W, p.nx - x0);
     const int c0 = VC * tx;              // first cell of this thread, within the segment
@@ -298,7 +273,10 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     // copies need no serialisation over lanes.
     const unsigned mbytes = (unsigned)min(W, p.pitch - x0);
     const unsigned sm0 = smem_u32(smask);
-    auto issue = [&](int k) {
+    // part 0: all ten copies; part 1..3 (the split issue of a 128-thread
+    // block): warp `part` issues planes 3(part-1) .. 3(part-1)+2, warp 1 also
+    // the expected byte count and the mask row
+    auto issue = [&](int k, int part) {
         if (lane != 0) return;
         const int s = k % kStages;
         const unsigned bar = bar0 + 8u * s;
@@ -323,17 +301,25 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
             if (sr >= 0) bytes += cbytes;
         }
         if (MASK && ok) bytes += mbytes;
-        mbar_expect_tx(bar, bytes);
+        if (part <= 1) mbar_expect_tx(bar, bytes);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int sr = srow[ey(i) == 0 ? 0 : (ey(i) > 0 ? 1 : 2)];
-            if (sr >= 0)
+            if (sr >= 0 && (part == 0 || i / 3 == part - 1))
                 bulk_g2s(st0 + (unsigned)(((s * 9 + i) * SW + dshift) * sizeof(T)),
                          fin + (i * pl + (I)sr * rs + wstart), cbytes, bar);
         }
-        if (MASK && ok)
+        if (MASK && ok && part <= 1)
             bulk_g2s(sm0 + (unsigned)(s * W), p.lmask + ((I)rr * pitch + x0), mbytes, bar);
     };
+    // which warps issue, and their part
+#ifndef LBM_SPLIT_ISSUE
+#define LBM_SPLIT_ISSUE 0
+#endif
+    constexpr bool kSplit = LBM_SPLIT_ISSUE && BXT == 128;
+    const int wid = tx >> 5;
+    const bool issuer = kSplit ? wid >= 1 : wid == kIssueWarp;
+    const int ipart = kSplit ? wid : 0;
 
     // populations g[i][j] of my VC cells (row rr) from stage s.  Fast: vector
     // shared loads.  Otherwise cell by cell: shared loads for a fluid cell
@@ -406,8 +392,8 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         mbar_init_fence();
     }
     __syncthreads();
-    if ((tx >> 5) == kIssueWarp)
-        for (int k = 0; k < kStages && k < nit; ++k) issue(k);
+    if (issuer)
+        for (int k = 0; k < kStages && k < nit; ++k) issue(k, ipart);
 
     unsigned sbp[VC];     // link bits of the previous row's cells
     bool fastp = false;   // its fast-path flag
@@ -508,9 +494,9 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         }
 
         // 3. refill the stage of row k (now in registers) with row k+kStages
-        if ((tx >> 5) == kIssueWarp && k + kStages < nit) {
+        if (issuer && k + kStages < nit) {
             fence_proxy_async();
-            issue(k + kStages);
+            issue(k + kStages, ipart);
         }
 
         // 4. collide the previous row
@@ -555,8 +541,8 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                     const float2 D = make_float2(dp[0], dp[1]);
                     const float2 Gx = make_float2(dxr[0], dxr[1]), Gy = make_float2(dyr[0], dyr[1]);
                     const float2 R = (SCH == 1 || (SCH == 2 && p.raw))
-                                         ? collide_raw<float>(SMEMP ? fresh_consts(p.cc) : CollConst<float>(p.cc), F, D, Gx, Gy)
-                                         : collide<float, SCH != 3>(SMEMP ? fresh_consts(p.cc) : CollConst<float>(p.cc), F, D, Gx, Gy);
+                                         ? collide_raw<float>(CollConst<float>(p.cc), F, D, Gx, Gy)
+                                         : collide<float, SCH != 3>(CollConst<float>(p.cc), F, D, Gx, Gy);
                     rho[0] = R.x;
                     rho[1] = R.y;
                     // A solid cell keeps its zeros.  Without a mask the only

@@ -26,8 +26,9 @@ LBM_ERR_CUDA = -3
 LBM_ERR_UNSTABLE = -4
 LBM_ERR_TIMEOUT = -5
 LBM_ERR_STATE = -6
-LBM_DIAG_COUNT = 7
-DIAG_NAMES = ("mass", "mom_x", "mom_y", "energy", "residual", "nonfinite", "step")
+LBM_DIAG_COUNT = 8
+DIAG_NAMES = ("mass", "mom_x", "mom_y", "energy", "residual", "nonfinite", "step",
+              "step_change")
 _STATUS = {0: "LBM_OK", -1: "LBM_ERR_INVALID", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA",
            -4: "LBM_ERR_UNSTABLE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE"}
 
@@ -282,7 +283,7 @@ def lbm_set_f(h, N, f):
 
 
 def lbm_diagnostics(h):
-    """Returns (status, out[7]); LBM_ERR_UNSTABLE is reported, not raised."""
+    """Returns (status, out[LBM_DIAG_COUNT]); LBM_ERR_UNSTABLE is reported, not raised."""
     out = (ctypes.c_double * LBM_DIAG_COUNT)()
     st = lib.lbm_diagnostics(h, out)
     if st not in (LBM_OK, LBM_ERR_UNSTABLE):

@@ -17,50 +17,101 @@ def rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
 
 
-def setup(channels, n, hw, seed):
+def setup(channels, n, hw, seed, sum_noise=None):
     from paper_2103_02119_gb300 import lbm as L
+    h, w = hw if isinstance(hw, tuple) else (hw, hw)
     params = S.init_params(channels, seed=seed)
-    params = [(S.bf16(w), S.bf16(b)) for w, b in params]  # representable on both sides
+    params = [(S.bf16(w_), S.bf16(b)) for w_, b in params]  # representable on both sides
     rng = np.random.default_rng(seed + 1)
-    x = S.bf16(rng.standard_normal((n, hw, hw, 4)))
-    t = rng.standard_normal((n, hw, hw, 3))
-    fluid = rng.random((n, hw, hw)) > 0.15
-    nn = L.lbm_nn_create(channels, n, hw, hw, seed=0)
+    x = S.bf16(rng.standard_normal((n, h, w, 4)))
+    x[..., 0] = rng.random((n, h, w)) > 0.85          # the solid flag of the output stage
+    t = rng.standard_normal((n, h, w, 3))
+    fluid = x[..., 0] < 0.5
+    nn = L.lbm_nn_create(channels, n, h, w, seed=0)
     L.lbm_nn_set_params(nn, L.params_to_vec(params).astype(np.float32))
     ref = S.WarmNet(channels, params, bf16_storage=True)
-    return L, nn, ref, x, t, fluid
+    noisy = S.WarmNet(channels, params, bf16_storage=True, sum_noise=sum_noise)
+    return L, nn, ref, noisy, x, t, fluid
 
 
-@pytest.mark.parametrize("channels,n,hw", [([8, 16], 2, 16), ([8, 16, 24], 3, 24),
-                                           ([32, 64, 128, 256], 2, 32)])
-def test_forward_matches_reference(channels, n, hw):
-    L, nn, ref, x, _, _ = setup(channels, n, hw, seed=1)
+def outliers(got, want, rtol=2.0 ** -7, atol_rms=2.0 ** -8):
+    """Elements outside |got - want| <= rtol |want| + atol_rms rms(want): an
+    FP32 accumulation differs from the FP64 one by ~1e-7, so got and want
+    agree to that except where a stored value's bfloat16 rounding (relative
+    step 2^-8) fell the other way, or a ReLU decided the other way; such an
+    element and those it feeds differ by about one bfloat16 step."""
+    got, want = np.ravel(got).astype(np.float64), np.ravel(want)
+    rms = float(np.sqrt(np.mean(want ** 2))) or 1e-30
+    return int(np.count_nonzero(np.abs(got - want) > rtol * np.abs(want) + atol_rms * rms))
+
+
+def allowed(n):
+    return max(1, n // 1000)  # 0.1 % of a tensor's elements, at least one
+
+
+# Shallow networks: borders (odd sizes), channel counts that are not multiples
+# of 8, several 64-wide output tiles, and several pixel splits of the weight
+# gradient (more than 4096 pixels).
+SHALLOW = [([8, 16], 2, 16), ([8, 16, 24], 3, 24), ([12], 2, (13, 19)), ([12, 20], 2, (14, 22)),
+           ([40, 72], 2, 32), ([16, 32], 3, 48)]
+
+
+@pytest.mark.parametrize("channels,n,hw", SHALLOW)
+def test_forward_matches_reference_elementwise(channels, n, hw):
+    L, nn, ref, _, x, _, _ = setup(channels, n, hw, seed=1)
     y = L.lbm_nn_forward(nn, x)
     yr, _ = ref.forward(x)
     assert y.shape == yr.shape
-    assert rel(y, yr) < 1e-2, rel(y, yr)
+    assert outliers(y, yr) <= allowed(yr.size), (outliers(y, yr), yr.size)
     L.lbm_nn_destroy(nn)
 
 
-@pytest.mark.parametrize("channels,n,hw", [([8, 16], 2, 16), ([8, 16, 24], 3, 24),
-                                           ([32, 64, 128, 256], 2, 32)])
-def test_gradients_match_reference(channels, n, hw):
-    L, nn, ref, x, t, fluid = setup(channels, n, hw, seed=2)
+@pytest.mark.parametrize("channels,n,hw", SHALLOW)
+def test_gradients_match_reference_elementwise(channels, n, hw):
+    L, nn, ref, _, x, t, fluid = setup(channels, n, hw, seed=2)
     loss, g = L.lbm_nn_gradients(nn, x, t, fluid)
     yr, tape = ref.forward(x)
     lr, gy = ref.loss(yr, t, fluid)
     gr = ref.backward(tape, gy)
     assert abs(loss - lr) <= 2e-3 * lr
-    shapes = S.layer_shapes(channels)
-    got = L.params_to_list(g, shapes)
+    got = L.params_to_list(g, S.layer_shapes(channels))
     for k, ((gw, gb), (rw, rb)) in enumerate(zip(got, gr)):
-        assert rel(gw, rw) < 3e-2, (k, rel(gw, rw))
-        assert rel(gb, rb) < 3e-2, (k, rel(gb, rb))
+        assert outliers(gw, rw) <= allowed(rw.size), (k, "w", outliers(gw, rw), rw.size)
+        assert outliers(gb, rb) <= allowed(rb.size), (k, "b", outliers(gb, rb), rb.size)
+    L.lbm_nn_destroy(nn)
+
+
+def test_deep_network_against_calibrated_reference():
+    """The production shape (4 levels, 32-256 channels) at 32 x 32: its
+    deepest layers sum over a few dozen pixels, so one flipped bfloat16
+    rounding or ReLU decision moves a visible share of an element.  The bound
+    is calibrated on the reference itself: the same network with its
+    convolution sums perturbed at the size of an FP32 accumulation error
+    (sum_noise) departs from the exact reference by a number of elements;
+    the kernels may depart by at most twice that (plus 0.1 %), tensor by
+    tensor, and the outputs by no more than 0.5 %."""
+    channels, n, hw = [32, 64, 128, 256], 2, 32
+    L, nn, ref, noisy, x, t, fluid = setup(channels, n, hw, seed=2, sum_noise=11)
+    y = L.lbm_nn_forward(nn, x)
+    yr, tape = ref.forward(x)
+    assert outliers(y, yr, atol_rms=2.0 ** -6) <= 0.005 * yr.size
+    loss, g = L.lbm_nn_gradients(nn, x, t, fluid)
+    lr, gy = ref.loss(yr, t, fluid)
+    gr = ref.backward(tape, gy)
+    yn, tape_n = noisy.forward(x)
+    _, gyn = noisy.loss(yn, t, fluid)
+    gn = noisy.backward(tape_n, gyn)
+    got = L.params_to_list(g, S.layer_shapes(channels))
+    for k in range(len(gr)):
+        for j, name in ((0, "w"), (1, "b")):
+            base = outliers(gn[k][j], gr[k][j])
+            mine = outliers(got[k][j], gr[k][j])
+            assert mine <= 2 * base + allowed(gr[k][j].size), (k, name, mine, base)
     L.lbm_nn_destroy(nn)
 
 
 def test_adam_step_matches_reference():
-    L, nn, ref, x, t, fluid = setup([8, 16], 2, 16, seed=3)
+    L, nn, ref, _, x, t, fluid = setup([8, 16], 2, 16, seed=3)
     p0 = L.lbm_nn_get_params(nn).astype(np.float64)
     _, g = L.lbm_nn_gradients(nn, x, t, fluid)
     lr = 1e-3
@@ -72,7 +123,7 @@ def test_adam_step_matches_reference():
 
 
 def test_training_reduces_the_loss():
-    L, nn, _, x, _, fluid = setup([8, 16], 2, 16, seed=4)
+    L, nn, _, _, x, _, fluid = setup([8, 16], 2, 16, seed=4)
     # a smooth target the network can fit
     yy, xx = np.meshgrid(np.linspace(0, 1, 16), np.linspace(0, 1, 16), indexing="ij")
     t = np.stack([np.sin(3 * xx) * yy, xx * yy, np.cos(2 * yy)], axis=-1)[None].repeat(2, 0)
@@ -93,11 +144,18 @@ def test_batch_size_limits():
 
 def test_warm_start_against_rest_start(orc):
     """A network trained on solver-generated steady cavities starts new
-    instances; the unmodified scheme finishes them to the same residual.  The
-    warm-started final fields describe the same flow as the rest-started ones
-    and stay steady under the FP64 oracle.  The steps either way are reported
-    (the gain is not asserted: at the accuracy reached here the warm start
-    needs more steps, see the design notes)."""
+    instances; the unmodified scheme finishes them to the same steady
+    residual (two-step means, R <= 1e-8).  Started from the prediction, every
+    instance settles on the state the rest start settles on: their two-step
+    mean velocities agree element by element within 1e-4 of the lid speed
+    (the residual bound leaves a slow drift of the order of R / rate of the
+    slowest mode, ~1e-5 U, in either run, and the FP32 rounding of two
+    different paths adds ~1e-6 U; measured 1e-6 to 7e-6 U).  Without the
+    network's output stage, which gives the prediction no staggered momentum
+    (an exact invariant of the scheme, lbm.h), the two differ by up to 12 %.
+    The warm-started state of two instances is then taken, from the same
+    start, to the same residual by the FP64 oracle.  The steps either way are
+    printed; the gain is measured by bench.py, not asserted here."""
     from paper_2103_02119_gb300 import warmstart as WS
     n = 32
     wls, x, t, fl, _ = WS.build_dataset(128, seed=0, n=n, max_steps=200_000)
@@ -108,40 +166,43 @@ def test_warm_start_against_rest_start(orc):
     test = WS.cavity_set(8, seed=1, n=n)
     y = ws.predict(WS.inputs_of(test))
     assert np.isfinite(y).all()
-    rest = WS.solve(test, max_steps=200_000)
-    warm = WS.solve(test, inits=[WS.fields_of(w, y[k]) for k, w in enumerate(test)],
-                    max_steps=400_000)
+    inits = [WS.fields_of(w, y[k]) for k, w in enumerate(test)]
+    rest = WS.solve(test, max_steps=400_000)
+    warm = WS.solve(test, inits=inits, max_steps=400_000)
     for res in (rest, warm):
         assert np.all((res["residual"] >= 0) & (res["residual"] <= 1e-8))
     print("steps rest", rest["steps"].tolist(), "warm", warm["steps"].tolist())
-    # Both runs meet the residual test, yet their final fields agree only to
-    # a few per cent (relative L2): the start from the prediction excites
-    # slowly decaying components that the residual test does not resolve
-    # (these runs also take many more steps).  The bound checks the two
-    # describe the same flow.
     for k, w in enumerate(test):
         fluid = w.mask == 0
-        a = np.stack(rest["fields"][k][1:])[:, fluid]
-        b = np.stack(warm["fields"][k][1:])[:, fluid]
-        rel = np.linalg.norm(a - b) / np.linalg.norm(a)
-        print("instance", k, "relative difference rest vs warm", rel)
-        assert rel <= 0.25, (k, rel)
-    # the warm-started steady state of one instance under the FP64 oracle
-    from paper_2103_02119_gb300.lbm import Batch
-    w = test[0]
-    b = Batch([w])
-    b.init_fields(0, *WS.fields_of(w, y[0]))
-    b.run(1e-8, check_every=100, max_steps=400_000)
-    f = b.get_f(0)
-    _, ug, vg = b.moments(0)
-    b.close()
-    p = orc.OracleParams.make(w.nx, w.ny, w.a, w.cs2, w.omega, periodic_x=0, periodic_y=0,
-                              wall_u=w.wall_u)
-    o = orc.Oracle(p, w.mask)
-    o.set_f(f)
-    o.step(200)
-    _, uo, vo = o.moments()
-    fluid = o.solid() == 0
-    assert np.abs(uo - ug)[fluid].max() < 1e-3 * w.info["U"]
-    assert np.abs(vo - vg)[fluid].max() < 1e-3 * w.info["U"]
+        a = np.stack(rest["mean_fields"][k][1:])[:, fluid]
+        b = np.stack(warm["mean_fields"][k][1:])[:, fluid]
+        d = float(np.abs(a - b).max()) / w.info["U"]
+        print("instance", k, "max |du| / U rest vs warm", d)
+        assert d <= 1e-4, (k, d)
+    # the FP64 oracle from the same warm start to the same residual
+    for k in (0, 1):
+        w = test[k]
+        p = orc.OracleParams.make(w.nx, w.ny, w.a, w.cs2, w.omega, periodic_x=0, periodic_y=0,
+                                  wall_u=w.wall_u)
+        o = orc.Oracle(p, w.mask)
+        o.init_fields(*inits[k])
+        fluid = o.solid() == 0
+        prev, R, steps = None, 1.0, 0
+        while steps < 400_000:
+            o.step(99)
+            _, u0, v0 = o.moments()
+            o.step(1)
+            steps += 100
+            _, u1, v1 = o.moments()
+            mean = np.stack([0.5 * (u0 + u1), 0.5 * (v0 + v1)])[:, fluid]
+            if prev is not None:
+                R = np.linalg.norm(mean - prev) / (100 * np.linalg.norm(mean))
+                if R <= 1e-8:
+                    break
+            prev = mean
+        assert R <= 1e-8, (k, steps, R)
+        g = np.stack(warm["mean_fields"][k][1:])[:, fluid]
+        d = float(np.abs(mean - g).max()) / w.info["U"]
+        print("instance", k, "oracle steps", steps, "max |du| / U GPU vs oracle", d)
+        assert d <= 1e-4, (k, d)
     ws.close()

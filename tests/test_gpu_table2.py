@@ -7,7 +7,8 @@ other to well under 1 %."""
 import numpy as np
 import pytest
 
-from test_oracle_table2 import channel, global_error, oracle_error, steps_for
+from gpu_common import F64_RTOL_U
+from test_oracle_table2 import channel, global_error, oracle_fields, steps_for
 
 pytestmark = pytest.mark.gpu
 
@@ -24,23 +25,28 @@ def gpu_fields(N, scheme):
 
 
 @pytest.fixture(scope="module")
-def errors():
+def runs():
     out = {}
     for N in (100, 200, 400):
         for s in ("rc", "rnr"):
-            u, v, ua = gpu_fields(N, s)
-            out[(N, s)] = global_error(u, v, ua)
-    print("Table 2 (GPU FP64):", {f"{N} {s}": f"{e:.3e}" for (N, s), e in out.items()})
+            out[(N, s)] = gpu_fields(N, s)
+    print("Table 2 (GPU FP64):",
+          {f"{N} {s}": f"{global_error(*f):.3e}" for (N, s), f in out.items()})
     return out
 
 
 @pytest.mark.parametrize("scheme", ["rc", "rnr"])
-def test_n100_matches_the_oracle(orc, errors, scheme):
-    e_orc = oracle_error(orc, 100, scheme)
-    assert abs(errors[(100, scheme)] - e_orc) <= 1e-9 * e_orc
+def test_n100_matches_the_oracle(orc, runs, scheme):
+    """Element by element after 110,000 steps (FP64 on both sides: only the
+    order of rounding differs)."""
+    u, v, ua = runs[(100, scheme)]
+    uo, vo, _ = oracle_fields(orc, 100, scheme)
+    du = max(np.abs(u - uo).max(), np.abs(v - vo).max()) / np.abs(uo).max()
+    assert du <= F64_RTOL_U, du
 
 
-def test_second_order_and_schemes_agree(errors):
+def test_second_order_and_schemes_agree(runs):
+    errors = {k: global_error(*f) for k, f in runs.items()}
     for s in ("rc", "rnr"):
         for N in (100, 200):
             ratio = errors[(N, s)] / errors[(2 * N, s)]

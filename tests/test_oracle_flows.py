@@ -211,3 +211,64 @@ def test_boosted_sound_wave_damping(orc, a, tol):
     rm = sound_damping(orc, a, cs2, 0.02, 64, -0.02)
     assert abs(r0 - 1) < 0.01
     assert abs(rp - rm) / r0 < tol
+
+
+def _staggered(o, n):
+    r, u, v = o.moments()
+    fl = o.solid() == 0
+    yy, xx = np.mgrid[0:u.shape[0], 0:u.shape[1]]
+    s = (-1.0) ** n
+    return (s * ((-1.0) ** xx * r * u * fl).sum(), s * ((-1.0) ** yy * r * v * fl).sum(),
+            (np.abs(r * u) + np.abs(r * v))[fl].sum())
+
+
+@pytest.mark.parametrize("walls", [0, 1])
+def test_staggered_momenta_are_exact_invariants(orc, walls):
+    """Besides the mass, the scheme keeps two staggered momenta exactly:
+    G_x = sum (-1)^(x+n) rho u_x and G_y = sum (-1)^(y+n) rho u_y over the
+    fluid cells (even nx, ny).  Streaming moves the populations that carry
+    them one cell (or bounces them back, half-way) and flips the sign of the
+    weight; the collision conserves momentum.  Checked on a periodic box and
+    on a closed box with obstacles (stationary walls), from a noisy start."""
+    n = 32
+    wl = W.cavity(n, 24, 0.7, W.stable_cs2(0.7), 0.0, 50.0)
+    mask = W.random_obstacles(n, 24, seed=7) if walls else None
+    p = orc.OracleParams.make(n, 24, wl.a, wl.cs2, wl.omega, periodic_x=1 - walls,
+                              periodic_y=1 - walls, nthreads=1)
+    o = orc.Oracle(p, mask)
+    r0, u0, v0 = W.smooth_random_fields(n, 24, seed=3, u_amp=0.03)
+    rng = np.random.default_rng(1)
+    o.init_fields(r0, u0 + 0.01 * rng.standard_normal(u0.shape),
+                  v0 + 0.01 * rng.standard_normal(v0.shape))
+    gx0, gy0, scale = _staggered(o, 0)
+    assert abs(gx0) > 1e-3 * scale and abs(gy0) > 1e-3 * scale
+    done = 0
+    for step in (1, 2, 10, 300):
+        o.step(step - done)
+        done = step
+        gx, gy, _ = _staggered(o, step)
+        assert abs(gx - gx0) <= 1e-12 * scale and abs(gy - gy0) <= 1e-12 * scale, (step, gx, gy)
+
+
+def test_longitudinal_nyquist_velocity_never_decays(orc):
+    """The carrier of G_y: u_y = A (-1)^y, uniform along x, is an equilibrium
+    state that streaming maps to minus itself, so it alternates forever; the
+    transverse (shear) pattern u_x = A (-1)^y decays at once.  This is why
+    the steady residual is taken on two-step means."""
+    n, a = 32, 0.5
+    cs2 = W.stable_cs2(a)
+    yy, xx = np.mgrid[0:n, 0:n]
+    amp = {}
+    for name, (u0, v0) in {"long": (0 * yy, 0.01 * (-1.0) ** yy),
+                           "shear": (0.01 * (-1.0) ** yy, 0 * yy)}.items():
+        p = orc.OracleParams.make(n, n, a, cs2, W.omega_for(0.01, cs2), nthreads=1)
+        o = orc.Oracle(p)
+        o.init_fields(np.ones((n, n)), u0.astype(float), v0.astype(float))
+        o.step(101)
+        _, u, v = o.moments()
+        amp[name] = (u, v)
+    u, v = amp["long"]
+    np.testing.assert_allclose(v, -0.01 * (-1.0) ** yy, rtol=0, atol=1e-12)
+    assert np.abs(u).max() < 1e-12
+    u, v = amp["shear"]
+    assert max(np.abs(u).max(), np.abs(v).max()) < 1e-12

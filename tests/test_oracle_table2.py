@@ -52,7 +52,7 @@ def global_error(u, v, ua):
     return float(np.sqrt((u - ua) ** 2 + v ** 2).sum() / np.abs(ua).sum())
 
 
-def oracle_error(orc, N, scheme):
+def oracle_fields(orc, N, scheme):
     wl, ua = channel(N)
     p = orc.OracleParams.make(wl.nx, wl.ny, A, CS2, wl.omega, Fx=wl.Fx, periodic_x=1,
                               periodic_y=0, scheme=scheme)
@@ -60,7 +60,11 @@ def oracle_error(orc, N, scheme):
     o.init_fields(np.ones_like(ua), ua, np.zeros_like(ua))
     o.step(steps_for(N))
     _, u, v = o.moments()
-    return global_error(u, v, ua)
+    return u, v, ua
+
+
+def oracle_error(orc, N, scheme):
+    return global_error(*oracle_fields(orc, N, scheme))
 
 
 @pytest.fixture(scope="module")

@@ -126,3 +126,51 @@ def test_first_adam_step_closed_form():
     # first step: m_hat = g, v_hat = g^2, so the update is lr g / (|g| + eps)
     assert np.allclose(q, p - 1e-2 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_output_stage_maps_are_self_adjoint_and_remove_staggered_content():
+    """The fixed output stage: smooth() and unstagger() are self-adjoint (so
+    the backward pass is the same maps in reverse order), unstagger() is a
+    projection whose result carries no staggered momentum over the fluid
+    cells, and smooth() annihilates the grid-scale patterns (-1)^x and
+    (-1)^y away from walls and solids."""
+    rng = np.random.default_rng(7)
+    a = rng.standard_normal((2, 12, 10, 3))
+    b = rng.standard_normal((2, 12, 10, 3))
+    fluid = rng.random((2, 12, 10)) > 0.2
+    for f in (S.smooth, S.unstagger):
+        assert np.isclose((f(a, fluid) * b).sum(), (a * f(b, fluid)).sum(), rtol=1e-13)
+    p = S.unstagger(a, fluid)
+    np.testing.assert_allclose(S.unstagger(p, fluid), p, atol=1e-13)
+    yy, xx = np.mgrid[0:12, 0:10]
+    for k in range(2):
+        m = fluid[k]
+        assert abs(((-1.0) ** xx * m * p[k, :, :, 1]).sum()) < 1e-12
+        assert abs(((-1.0) ** yy * m * p[k, :, :, 2]).sum()) < 1e-12
+    np.testing.assert_array_equal(p[..., 0], a[..., 0])
+    allf = np.ones((1, 12, 10), bool)
+    z = np.zeros((1, 12, 10, 3))
+    z[0, :, :, 1] = (-1.0) ** xx
+    z[0, :, :, 2] = (-1.0) ** yy
+    s = S.smooth(z, allf)
+    assert np.abs(s[0, 1:-1, 1:-1, 1:]).max() < 1e-15
+    # a smooth field passes with an O(h^2) change
+    sm = np.zeros((1, 12, 10, 3))
+    sm[0, :, :, 0] = np.sin(2 * np.pi * xx / 10) * np.cos(np.pi * yy / 12)
+    d = S.smooth(sm, allf) - sm
+    assert np.abs(d[0, 1:-1, 1:-1, 0]).max() < 0.12
+
+
+def test_output_stage_in_the_network_forward():
+    channels = [4, 8]
+    net = S.WarmNet(channels, S.init_params(channels, seed=5))
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((2, 8, 8, 4))
+    x[..., 0] = rng.random((2, 8, 8)) > 0.8
+    y, tape = net.forward(x)
+    fluid = x[..., 0] < 0.5
+    assert np.all(y[~fluid] == 0)
+    yy, xx = np.mgrid[0:8, 0:8]
+    for k in range(2):
+        assert abs(((-1.0) ** xx * fluid[k] * y[k, :, :, 1]).sum()) < 1e-12
+        assert abs(((-1.0) ** yy * fluid[k] * y[k, :, :, 2]).sum()) < 1e-12
