@@ -68,6 +68,10 @@ def parse():
                     help="skip the learned warm-start measurement")
     ap.add_argument("--warm-train", type=int, default=1024)
     ap.add_argument("--warm-epochs", type=int, default=60)
+    ap.add_argument("--config4-ttr", action="store_true",
+                    help="only the time to R <= 1e-8 of the full 512-lattice sweep under a "
+                         "step cap, batched against sequential (minutes)")
+    ap.add_argument("--ttr-cap", type=int, default=20000)
     ap.add_argument("--block-x", type=int, default=0)
     ap.add_argument("--bands", type=int, default=0)
     return ap.parse_args()
@@ -379,6 +383,60 @@ def batch_time_to_residual(torch, count, max_steps, tol=1e-8, check=100):
             "sequential_max_steps": max(steps_s), "speedup": ts / tb}
 
 
+def config4_time_to_residual(torch, count=512, cap=20000, tol=1e-8, check=100):
+    """The full batched sweep (the batch_throughput recipe, seed 0) from rest
+    to R <= tol under a cap of `cap` steps per lattice: the batch (autotune +
+    run with retirement) against the same lattices one after another (an
+    lbm_step / lbm_diagnostics loop each).  Lattices not converged at the cap
+    are listed with their last residual."""
+    import numpy as np
+    from paper_2103_02119_gb300 import workloads as W
+    from paper_2103_02119_gb300.lbm import Batch, Lattice
+    stream = torch.cuda.current_stream()
+    ws = W.batch_sweep(count, seed=0)
+    b = Batch(ws, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    shape = b.tune(trial_steps=5)
+    st, res = b.run(tol, check_every=check, max_steps=cap)
+    tb = time.perf_counter() - t0
+    steps_b = [b.step_count(k) for k in range(count)]
+    b.close()
+    conv_b = [bool(0 <= r <= tol) for r in res]
+    ts, res_s, steps_s = 0.0, [], []
+    for w in ws:
+        lat = Lattice.from_workload(w, precision=32, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.diagnostics()
+        n, R = 0, -1.0
+        while n < cap:
+            lat.step(check)
+            n += check
+            _, d = lat.diagnostics()
+            R = d[4]
+            if not np.isfinite(R) or 0 <= R <= tol:
+                break
+        ts += time.perf_counter() - t0
+        res_s.append(float(R))
+        steps_s.append(n)
+        lat.close()
+    conv_s = [bool(0 <= r <= tol) for r in res_s]
+    cells = sum(w.cells for w in ws)
+    return {"sample": f"all {count} lattices of the sweep (seed 0), {cells} cells, rest start",
+            "tol": tol, "check_every": check, "cap_steps": cap,
+            "shape": {"block_x": shape[0], "rows_per_band": shape[1]},
+            "batched_s": tb, "batched_converged": sum(conv_b),
+            "batched_lattice_steps": int(sum(steps_b)),
+            "sequential_s": ts, "sequential_converged": sum(conv_s),
+            "sequential_lattice_steps": int(sum(steps_s)),
+            "speedup": ts / tb,
+            "not_converged": [{"k": k, "nx": ws[k].nx, "ny": ws[k].ny,
+                               "Re": round(ws[k].info["Re"], 1), "kind": ws[k].info["kind"],
+                               "R_batched": float(res[k]), "R_sequential": res_s[k]}
+                              for k in range(count) if not (conv_b[k] and conv_s[k])]}
+
+
 # ------------------------------------------------------------ small lattice --
 
 def small_lattice(torch):
@@ -524,6 +582,11 @@ def main():
     if args.batch_only:
         if rank == 0:
             print(json.dumps(batch_throughput(torch, args.batch_count, args.batch_steps)),
+                  flush=True)
+        return
+    if args.config4_ttr:
+        if rank == 0:
+            print(json.dumps(config4_time_to_residual(torch, args.batch_count, args.ttr_cap)),
                   flush=True)
         return
 

@@ -273,10 +273,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     // copies need no serialisation over lanes.
     const unsigned mbytes = (unsigned)min(W, p.pitch - x0);
     const unsigned sm0 = smem_u32(smask);
-    // part 0: all ten copies; part 1..3 (the split issue of a 128-thread
-    // block): warp `part` issues planes 3(part-1) .. 3(part-1)+2, warp 1 also
-    // the expected byte count and the mask row
-    auto issue = [&](int k, int part) {
+    auto issue = [&](int k) {
         if (lane != 0) return;
         const int s = k % kStages;
         const unsigned bar = bar0 + 8u * s;
@@ -301,25 +298,20 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
             if (sr >= 0) bytes += cbytes;
         }
         if (MASK && ok) bytes += mbytes;
-        if (part <= 1) mbar_expect_tx(bar, bytes);
+        mbar_expect_tx(bar, bytes);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int sr = srow[ey(i) == 0 ? 0 : (ey(i) > 0 ? 1 : 2)];
-            if (sr >= 0 && (part == 0 || i / 3 == part - 1))
+            if (sr >= 0)
                 bulk_g2s(st0 + (unsigned)(((s * 9 + i) * SW + dshift) * sizeof(T)),
                          fin + (i * pl + (I)sr * rs + wstart), cbytes, bar);
         }
-        if (MASK && ok && part <= 1)
+        if (MASK && ok)
             bulk_g2s(sm0 + (unsigned)(s * W), p.lmask + ((I)rr * pitch + x0), mbytes, bar);
     };
-    // which warps issue, and their part
-#ifndef LBM_SPLIT_ISSUE
-#define LBM_SPLIT_ISSUE 0
-#endif
-    constexpr bool kSplit = LBM_SPLIT_ISSUE && BXT == 128;
-    const int wid = tx >> 5;
-    const bool issuer = kSplit ? wid >= 1 : wid == kIssueWarp;
-    const int ipart = kSplit ? wid : 0;
+    // (spreading the ten copies over warps 1-3 measured 5 % slower than one
+    // lane of one warp issuing them all)
+    const bool issuer = (tx >> 5) == kIssueWarp;
 
     // populations g[i][j] of my VC cells (row rr) from stage s.  Fast: vector
     // shared loads.  Otherwise cell by cell: shared loads for a fluid cell
@@ -393,7 +385,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     }
     __syncthreads();
     if (issuer)
-        for (int k = 0; k < kStages && k < nit; ++k) issue(k, ipart);
+        for (int k = 0; k < kStages && k < nit; ++k) issue(k);
 
     unsigned sbp[VC];     // link bits of the previous row's cells
     bool fastp = false;   // its fast-path flag
@@ -496,7 +488,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         // 3. refill the stage of row k (now in registers) with row k+kStages
         if (issuer && k + kStages < nit) {
             fence_proxy_async();
-            issue(k + kStages, ipart);
+            issue(k + kStages);
         }
 
         // 4. collide the previous row
