@@ -62,6 +62,8 @@ def parse():
                     help="run only the batched-sweep throughput (for profiling)")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--batch-shape", default="",
+                    help="BX,ROWS: a fixed launch shape instead of the autotuner's")
     ap.add_argument("--ttr-count", type=int, default=64)
     ap.add_argument("--ttr-max-steps", type=int, default=60000)
     ap.add_argument("--no-warm", action="store_true",
@@ -294,7 +296,7 @@ def e2e(lat, wl, torch, chunk, reps):
 
 # ------------------------------------------------------------ batched sweep --
 
-def batch_throughput(torch, count, steps):
+def batch_throughput(torch, count, steps, fixed_shape=None):
     """One persistent launch per step over `count` uneven lattices, against
     the same lattices advanced one after another with the single-lattice
     step (one launch per lattice and step)."""
@@ -304,7 +306,11 @@ def batch_throughput(torch, count, steps):
     ws = W.batch_sweep(count, seed=0)
     cells = sum(w.cells for w in ws)
     b = Batch(ws, stream=stream)
-    shape = b.tune(trial_steps=10)
+    if fixed_shape:
+        b.set_shape(*fixed_shape)
+        shape = b.shape
+    else:
+        shape = b.tune(trial_steps=10)
     b.step(4)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -581,7 +587,8 @@ def main():
 
     if args.batch_only:
         if rank == 0:
-            print(json.dumps(batch_throughput(torch, args.batch_count, args.batch_steps)),
+            shape = tuple(int(v) for v in args.batch_shape.split(",")) if args.batch_shape else None
+            print(json.dumps(batch_throughput(torch, args.batch_count, args.batch_steps, shape)),
                   flush=True)
         return
     if args.config4_ttr:
