@@ -419,8 +419,8 @@ def config4_time_to_residual(torch, count=512, cap=20000, tol=1e-8, check=100):
         while n < cap:
             lat.step(check)
             n += check
-            _, d = lat.diagnostics()
-            R = d[4]
+            st, d = lat.diagnostics()
+            R = float("nan") if st != 0 else d[4]
             if not np.isfinite(R) or 0 <= R <= tol:
                 break
         ts += time.perf_counter() - t0
@@ -428,6 +428,7 @@ def config4_time_to_residual(torch, count=512, cap=20000, tol=1e-8, check=100):
         steps_s.append(n)
         lat.close()
     conv_s = [bool(0 <= r <= tol) for r in res_s]
+    unstable = [k for k in range(count) if not (np.isfinite(res[k]) and np.isfinite(res_s[k]))]
     cells = sum(w.cells for w in ws)
     return {"sample": f"all {count} lattices of the sweep (seed 0), {cells} cells, rest start",
             "tol": tol, "check_every": check, "cap_steps": cap,
@@ -436,7 +437,7 @@ def config4_time_to_residual(torch, count=512, cap=20000, tol=1e-8, check=100):
             "batched_lattice_steps": int(sum(steps_b)),
             "sequential_s": ts, "sequential_converged": sum(conv_s),
             "sequential_lattice_steps": int(sum(steps_s)),
-            "speedup": ts / tb,
+            "speedup": ts / tb, "unstable": unstable,
             "not_converged": [{"k": k, "nx": ws[k].nx, "ny": ws[k].ny,
                                "Re": round(ws[k].info["Re"], 1), "kind": ws[k].info["kind"],
                                "R_batched": float(res[k]), "R_sequential": res_s[k]}
