@@ -8,8 +8,9 @@
  * lbm_init_fields / lbm_batch_init_fields start the unmodified scheme.  Its
  * forward pass, backward pass and Adam update run as CUDA kernels: the 3x3
  * convolutions (forward, input gradient, weight gradient) as implicit GEMMs
- * on the BF16 tensor cores (mma.sync m16n8k16, FP32 accumulation); pooling,
- * upsampling, skip additions, the loss and the optimizer as plain kernels.
+ * on the fifth-generation tensor cores (tcgen05.mma with BF16 operands and an
+ * FP32 accumulator in tensor memory); pooling, upsampling, skip additions,
+ * the output stage, the loss and the optimizer as plain kernels.
  *
  * Network (levels l = 0 .. L-1, channels c[l]):
  *   encoder: x = relu(conv(x)); x = relu(conv(x)); e[l] = x;
@@ -43,7 +44,9 @@
  * (cout fastest) followed by its cout biases, as float.
  *
  * Conventions as in lbm.h: lbm_status returns, host arrays copied, work on
- * the stream given at creation; every call here is synchronous.
+ * the stream given at creation; every call here is synchronous.  Every wait
+ * of the tensor-core GEMMs is bounded: one that runs out leaves its tile
+ * unstored and the call returns LBM_ERR_TIMEOUT.
  */
 #ifndef LBM_GB300_NN_H
 #define LBM_GB300_NN_H

@@ -1,20 +1,24 @@
 // nn.cu -- the warm-start surrogate of include/lbm_nn.h: a 3x3-convolution
 // encoder-decoder trained and evaluated on the GPU.
 //
-// The three GEMMs of a convolution run on the BF16 tensor cores
-// (mma.sync.m16n8k16, FP32 accumulation) as implicit GEMMs over NHWC
-// activations with channels padded to a multiple of 8:
+// The three GEMMs of a convolution run on the fifth-generation tensor cores
+// (tcgen05.mma, kind::f16: BF16 operands from shared memory, FP32
+// accumulator in tensor memory) as implicit GEMMs over NHWC activations with
+// channels padded to a multiple of 8:
 //   forward      M = pixels, N = cout, K = 9 cin:
 //                A[p][(tap, ci)] = in(p + s(tap))[ci], B[co][(tap, ci)] = W
 //   input grad   M = pixels, N = cin, K = 9 cout:
 //                A[q][(tap, co)] = g(q - s(tap))[co], B[ci][(tap, co)] = W
-//   weight grad  M = cout, N = 9 cin, K = pixels (split over blocks, the
-//                partial sums added in a fixed order):
-//                A[co][p] = g(p)[co], B[(tap, ci)][p] = in(p + s(tap))[ci]
-// with s(tap) = (dy - 1, dx - 1) and zeros outside the grid.  A block
-// computes a 64 x 64 tile with four warps (32 x 32 each) over K chunks of 32
-// staged in shared memory as [row][k] with a padded stride, from which each
-// thread reads its fragments with 32-bit loads.
+//   weight grad  M = 9 cin, N = cout, K = pixels (split over blocks, the
+//                partial sums added in a fixed order), transposed so that the
+//                taps and input channels fill the 128 rows of the MMA:
+//                A[(tap, ci)][p] = in(p + s(tap))[ci], B[co][p] = g(p)[co]
+// with s(tap) = (dy - 1, dx - 1) and zeros outside the grid.  A CTA of 128
+// threads computes a 128 x N tile (N = 16 .. 256): the threads gather K
+// chunks of 64 into two shared-memory buffers in the tensor core's K-major
+// core-matrix layout, one thread issues the MMAs of a chunk and commits them
+// to the buffer's mbarrier, and each warp reads its 32 rows of the
+// accumulator back with tcgen05.ld.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -33,18 +37,8 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int BM = 64, BN = 64, BK = 32, LDS = BK + 8;
-constexpr int kGemmThreads = 128;
 constexpr int kThreads = 256;
 constexpr int kSplitPixels = 4096;  // pixels per block of the weight-gradient GEMM
-
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
-        "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 struct Geo {
     int n, h, w;          // batch and grid
@@ -61,7 +55,33 @@ __device__ __forceinline__ bool shifted(const Geo& g, long long p, int dy, int d
     return true;
 }
 
-// Forward: out = act(conv(in) + b).
+// ---- operand tiles of the tensor-core GEMM ----
+//
+// A tile holds rows r (of UM = 128 for A, BN for B) and the K chunk
+// [k0, k0 + UK) in the no-swizzle K-major layout of the tensor core's shared
+// memory descriptors: 8 x 8 core matrices of 8 rows by 16 bytes, stored
+// contiguously (128 bytes), the core matrices of one row group adjacent along
+// K (leading byte offset 128) and the row groups 8 core matrices apart
+// (stride byte offset 1024).
+constexpr int UM = 128, UK = 64, kGemmThreads = 128;
+constexpr unsigned kLBO = 128, kSBO = (UK / 8) * 128;
+
+__device__ __forceinline__ unsigned tile_off(int r, int kc) {
+    return (unsigned)(r >> 3) * kSBO + (unsigned)(kc >> 3) * kLBO + (unsigned)(r & 7) * 16 +
+           (unsigned)(kc & 7) * 2;
+}
+__device__ __forceinline__ void put8(unsigned char* t, int r, int kc, uint4 v) {
+    *reinterpret_cast<uint4*>(t + tile_off(r, kc)) = v;
+}
+// eight values along the rows r .. r+7 at one k (a transposed gather)
+__device__ __forceinline__ void put8_rows(unsigned char* t, int r, int kc, uint4 v) {
+    const bf16* e = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) *reinterpret_cast<bf16*>(t + tile_off(r + j, kc)) = e[j];
+}
+
+// Forward: out = act(conv(in) + b).  M = pixels, N = cout, K = 9 cin:
+// A[p][(tap, ci)] = in(p + s(tap))[ci], B[co][(tap, ci)] = W.
 struct FwdOp {
     Geo g;
     const bf16* in;    // [P][cin]
@@ -72,11 +92,12 @@ struct FwdOp {
     __host__ __device__ long long M() const { return g.P; }
     __host__ __device__ int N() const { return cout; }
     __host__ __device__ long long K() const { return 9LL * cin; }
-    __device__ void load_a(bf16* As, long long m0, long long k0, long long kend, int tid) const {
+    __device__ void load_a(unsigned char* t, long long m0, long long k0, long long kend,
+                           int tid) const {
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int v = tid + i * kGemmThreads, m = v >> 2, kq = (v & 3) * 8;
-            const long long p = m0 + m, k = k0 + kq;
+        for (int i = 0; i < UM * UK / 8 / kGemmThreads; ++i) {
+            const int v = tid + i * kGemmThreads, r = v >> 3, kc = (v & 7) * 8;
+            const long long p = m0 + r, k = k0 + kc;
             uint4 val = make_uint4(0, 0, 0, 0);
             if (p < g.P && k < kend) {
                 const int tap = (int)(k / cin), ci = (int)(k - (long long)tap * cin);
@@ -84,33 +105,39 @@ struct FwdOp {
                 if (shifted(g, p, tap / 3 - 1, tap % 3 - 1, q))
                     val = *reinterpret_cast<const uint4*>(in + q * cin + ci);
             }
-            *reinterpret_cast<uint4*>(As + m * LDS + kq) = val;
+            put8(t, r, kc, val);
         }
     }
-    __device__ void load_b(bf16* Bs, int n0, long long k0, long long kend, int tid) const {
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int v = tid + i * kGemmThreads, nn = v >> 2, kq = (v & 3) * 8;
-            const long long k = k0 + kq;
+    __device__ void load_b(unsigned char* t, int n0, long long k0, long long kend, int tid,
+                           int bn) const {
+        for (int v = tid; v < bn * (UK / 8); v += kGemmThreads) {
+            const int r = v >> 3, kc = (v & 7) * 8;
+            const long long k = k0 + kc;
             uint4 val = make_uint4(0, 0, 0, 0);
-            if (n0 + nn < cout && k < kend)
-                val = *reinterpret_cast<const uint4*>(wf + (long long)(n0 + nn) * K() + k);
-            *reinterpret_cast<uint4*>(Bs + nn * LDS + kq) = val;
+            if (n0 + r < cout && k < kend)
+                val = *reinterpret_cast<const uint4*>(wf + (long long)(n0 + r) * K() + k);
+            put8(t, r, kc, val);
         }
     }
-    __device__ void store(long long row, int col, float v0, float v1, int) const {
-        if (row >= g.P || col >= cout) return;
-        v0 += bias[col];
-        v1 += bias[col + 1];
-        if (relu) {
-            v0 = fmaxf(v0, 0.0f);
-            v1 = fmaxf(v1, 0.0f);
+    __device__ void store16(long long row, int col0, const float* v, int) const {
+        if (row >= g.P) return;
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+            const int col = col0 + j;
+            if (col >= cout) break;
+            float v0 = v[j] + bias[col], v1 = v[j + 1] + bias[col + 1];
+            if (relu) {
+                v0 = fmaxf(v0, 0.0f);
+                v1 = fmaxf(v1, 0.0f);
+            }
+            *reinterpret_cast<__nv_bfloat162*>(out + row * cout + col) =
+                __floats2bfloat162_rn(v0, v1);
         }
-        *reinterpret_cast<__nv_bfloat162*>(out + row * cout + col) = __floats2bfloat162_rn(v0, v1);
     }
 };
 
-// Input gradient: gin = conv^T(gpre).
+// Input gradient: gin = conv^T(gpre).  M = pixels, N = cin, K = 9 cout:
+// A[q][(tap, co)] = g(q - s(tap))[co], B[ci][(tap, co)] = W.
 struct DgradOp {
     Geo g;
     const bf16* gpre;  // [P][cout]
@@ -120,11 +147,12 @@ struct DgradOp {
     __host__ __device__ long long M() const { return g.P; }
     __host__ __device__ int N() const { return cin; }
     __host__ __device__ long long K() const { return 9LL * cout; }
-    __device__ void load_a(bf16* As, long long m0, long long k0, long long kend, int tid) const {
+    __device__ void load_a(unsigned char* t, long long m0, long long k0, long long kend,
+                           int tid) const {
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int v = tid + i * kGemmThreads, m = v >> 2, kq = (v & 3) * 8;
-            const long long p = m0 + m, k = k0 + kq;
+        for (int i = 0; i < UM * UK / 8 / kGemmThreads; ++i) {
+            const int v = tid + i * kGemmThreads, r = v >> 3, kc = (v & 7) * 8;
+            const long long p = m0 + r, k = k0 + kc;
             uint4 val = make_uint4(0, 0, 0, 0);
             if (p < g.P && k < kend) {
                 const int tap = (int)(k / cout), co = (int)(k - (long long)tap * cout);
@@ -132,138 +160,252 @@ struct DgradOp {
                 if (shifted(g, p, 1 - tap / 3, 1 - tap % 3, q))
                     val = *reinterpret_cast<const uint4*>(gpre + q * cout + co);
             }
-            *reinterpret_cast<uint4*>(As + m * LDS + kq) = val;
+            put8(t, r, kc, val);
         }
     }
-    __device__ void load_b(bf16* Bs, int n0, long long k0, long long kend, int tid) const {
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int v = tid + i * kGemmThreads, nn = v >> 2, kq = (v & 3) * 8;
-            const long long k = k0 + kq;
+    __device__ void load_b(unsigned char* t, int n0, long long k0, long long kend, int tid,
+                           int bn) const {
+        for (int v = tid; v < bn * (UK / 8); v += kGemmThreads) {
+            const int r = v >> 3, kc = (v & 7) * 8;
+            const long long k = k0 + kc;
             uint4 val = make_uint4(0, 0, 0, 0);
-            if (n0 + nn < cin && k < kend)
-                val = *reinterpret_cast<const uint4*>(wd + (long long)(n0 + nn) * K() + k);
-            *reinterpret_cast<uint4*>(Bs + nn * LDS + kq) = val;
+            if (n0 + r < cin && k < kend)
+                val = *reinterpret_cast<const uint4*>(wd + (long long)(n0 + r) * K() + k);
+            put8(t, r, kc, val);
         }
     }
-    __device__ void store(long long row, int col, float v0, float v1, int) const {
-        if (row >= g.P || col >= cin) return;
-        *reinterpret_cast<__nv_bfloat162*>(gin + row * cin + col) = __floats2bfloat162_rn(v0, v1);
+    __device__ void store16(long long row, int col0, const float* v, int) const {
+        if (row >= g.P) return;
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+            const int col = col0 + j;
+            if (col >= cin) break;
+            *reinterpret_cast<__nv_bfloat162*>(gin + row * cin + col) =
+                __floats2bfloat162_rn(v[j], v[j + 1]);
+        }
     }
 };
 
-// Weight gradient, one split of the pixels per blockIdx.z: part[z][co][(tap, ci)].
+// Weight gradient, transposed so that the taps and input channels (9 cin,
+// usually the larger side) fill the 128 rows: M = 9 cin, N = cout,
+// K = pixels (one split of them per blockIdx.z):
+// A[(tap, ci)][p] = in(p + s(tap))[ci], B[co][p] = g(p)[co];
+// part[z][co][(tap, ci)] = D[(tap, ci)][co].
 struct WgradOp {
     Geo g;
     const bf16* gpre;  // [P][cout]
     const bf16* in;    // [P][cin]
     float* part;       // [splits][cout][9 cin]
     int cin, cout;
-    __host__ __device__ long long M() const { return cout; }
-    __host__ __device__ int N() const { return 9 * cin; }
+    __host__ __device__ long long M() const { return 9LL * cin; }
+    __host__ __device__ int N() const { return cout; }
     __host__ __device__ long long K() const { return g.P; }
-    __device__ void load_a(bf16* As, long long m0, long long k0, long long kend, int tid) const {
+    __device__ void load_a(unsigned char* t, long long m0, long long k0, long long kend,
+                           int tid) const {
+        // items (row group of 8 channels, pixel): 16 x 64, consecutive
+        // threads on consecutive channel groups of one pixel
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int v = tid + i * kGemmThreads, kk = v >> 3, c8 = (v & 7) * 8;
-            const long long p = k0 + kk;
+        for (int i = 0; i < UM * UK / 8 / kGemmThreads; ++i) {
+            const int v = tid + i * kGemmThreads, grp = v & 15, kk = v >> 4;
+            const long long m = m0 + grp * 8, p = k0 + kk;
             uint4 val = make_uint4(0, 0, 0, 0);
-            if (p < kend && m0 + c8 < cout)
-                val = *reinterpret_cast<const uint4*>(gpre + p * cout + m0 + c8);
-            const bf16* e = reinterpret_cast<const bf16*>(&val);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) As[(c8 + j) * LDS + kk] = e[j];
-        }
-    }
-    __device__ void load_b(bf16* Bs, int n0, long long k0, long long kend, int tid) const {
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int v = tid + i * kGemmThreads, kk = v >> 3, c8 = (v & 7) * 8;
-            const long long p = k0 + kk;
-            const int n = n0 + c8;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (p < kend && n < N()) {
-                const int tap = n / cin, ci = n - tap * cin;
+            if (m < M() && p < kend) {
+                const int tap = (int)(m / cin), ci = (int)(m - (long long)tap * cin);
                 long long q;
                 if (shifted(g, p, tap / 3 - 1, tap % 3 - 1, q))
                     val = *reinterpret_cast<const uint4*>(in + q * cin + ci);
             }
-            const bf16* e = reinterpret_cast<const bf16*>(&val);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) Bs[(c8 + j) * LDS + kk] = e[j];
+            put8_rows(t, grp * 8, kk, val);
         }
     }
-    __device__ void store(long long row, int col, float v0, float v1, int z) const {
-        if (row >= cout || col >= N()) return;
-        float* d = part + ((long long)z * cout + row) * N() + col;
-        d[0] = v0;
-        d[1] = v1;
+    __device__ void load_b(unsigned char* t, int n0, long long k0, long long kend, int tid,
+                           int bn) const {
+        for (int v = tid; v < (bn / 8) * UK; v += kGemmThreads) {
+            const int grp = v % (bn / 8), kk = v / (bn / 8);
+            const int co = n0 + grp * 8;
+            const long long p = k0 + kk;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (co < cout && p < kend)
+                val = *reinterpret_cast<const uint4*>(gpre + p * cout + co);
+            put8_rows(t, grp * 8, kk, val);
+        }
+    }
+    __device__ void store16(long long row, int col0, const float* v, int z) const {
+        if (row >= M()) return;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int co = col0 + j;
+            if (co >= cout) break;
+            part[((long long)z * cout + co) * M() + row] = v[j];
+        }
     }
 };
 
-template <class Op>
-__global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const Op op, long long kchunk) {
-    __shared__ __align__(16) bf16 As[BM * LDS];
-    __shared__ __align__(16) bf16 Bs[BN * LDS];
-    const long long m0 = (long long)blockIdx.x * BM;
+// ---- the tensor-core GEMM: tcgen05.mma, accumulator in tensor memory ----
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+// shared memory matrix descriptor: start address, leading / stride byte
+// offsets (all >> 4), version 1 at bits 46-47, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// bounded wait on an mbarrier phase; false when it ran out
+__device__ __forceinline__ bool mbar_wait_parity(unsigned bar, unsigned parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int BN>
+__host__ __device__ constexpr int tmem_cols() { return BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256; }
+template <int BN>
+constexpr size_t umma_smem() { return 2 * (size_t)(UM + BN) * UK * 2 + 64; }
+
+// One CTA computes a UM x BN tile of D = A B^T over its K range: K chunks of
+// UK in two shared-memory buffers, four MMAs of K = 16 per chunk issued by
+// one thread and committed to the buffer's mbarrier, so that the threads
+// gather the next chunk while the tensor core works; the accumulator lives in
+// BN columns of tensor memory and is read back by each warp for its 32 rows.
+// Every wait is bounded; one that runs out sets *err and the tile is not
+// stored.
+template <class Op, int BN>
+__global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const Op op, long long kchunk,
+                                                                 int* err) {
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
+    extern __shared__ __align__(1024) unsigned char sm[];
+    // buffer b: A at sm + b UM UK 2, B at sm + 2 UM UK 2 + b BN UK 2
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * (UM + BN) * UK * 2);
+    unsigned* tslot = reinterpret_cast<unsigned*>(bars + 2);
+    constexpr int TC = tmem_cols<BN>();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long m0 = (long long)blockIdx.x * UM;
     const int n0 = blockIdx.y * BN;
     const long long kbeg = (long long)blockIdx.z * kchunk;
     const long long kend = min(op.K(), kbeg + kchunk);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int gq = lane >> 2, t = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
-    for (long long k0 = kbeg; k0 < kend; k0 += BK) {
-        op.load_a(As, m0, k0, kend, tid);
-        op.load_b(Bs, n0, k0, kend, tid);
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t a[2][4], b[4][2];
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi) {
-                const bf16* base = As + (wm + mi * 16 + gq) * LDS + kk + 2 * t;
-                a[mi][0] = *reinterpret_cast<const uint32_t*>(base);
-                a[mi][1] = *reinterpret_cast<const uint32_t*>(base + 8 * LDS);
-                a[mi][2] = *reinterpret_cast<const uint32_t*>(base + 8);
-                a[mi][3] = *reinterpret_cast<const uint32_t*>(base + 8 * LDS + 8);
-            }
-#pragma unroll
-            for (int ni = 0; ni < 4; ++ni) {
-                const bf16* bb = Bs + (wn + ni * 8 + gq) * LDS + kk + 2 * t;
-                b[ni][0] = *reinterpret_cast<const uint32_t*>(bb);
-                b[ni][1] = *reinterpret_cast<const uint32_t*>(bb + 8);
-            }
-#pragma unroll
-            for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni]);
-        }
-        __syncthreads();
+    const int nkb = kend > kbeg ? (int)((kend - kbeg + UK - 1) / UK) : 0;
+    const unsigned bar0 = smem_addr(bars);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(tslot)),
+                     "n"(TC)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned taddr = *tslot;
+    // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                               ((uint32_t)(UM >> 4) << 24);
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int b = kb & 1;
+        // the MMAs of chunk kb - 2 read this buffer
+        if (kb >= 2) ok &= mbar_wait_parity(bar0 + 8u * b, (unsigned)(((kb - 2) >> 1) & 1));
+        const long long k0 = kbeg + (long long)kb * UK;
+        unsigned char* At = sm + b * (UM * UK * 2);
+        unsigned char* Bt = sm + 2 * UM * UK * 2 + b * (BN * UK * 2);
+        op.load_a(At, m0, k0, kend, tid);
+        op.load_b(Bt, n0, k0, kend, tid, BN);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned a0 = smem_addr(At), b0 = smem_addr(Bt);
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
+            for (int kk = 0; kk < UK / 16; ++kk) {
+                const uint64_t ad = smem_desc(a0 + kk * 2 * kLBO, kLBO, kSBO);
+                const uint64_t bd = smem_desc(b0 + kk * 2 * kLBO, kLBO, kSBO);
+                const unsigned acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    bar0 + 8u * b)
+                : "memory");
+        }
+    }
+    // the last commit tracks every MMA of the tile
+    if (nkb > 0)
+        ok &= mbar_wait_parity(bar0 + 8u * ((nkb - 1) & 1), (unsigned)(((nkb - 1) >> 1) & 1));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const long long row = m0 + 32 * warp + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr + ((unsigned)(32 * warp) << 16) + (unsigned)c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float v[16];
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh)
-                op.store(m0 + wm + mi * 16 + gq + 8 * hh, n0 + wn + ni * 8 + 2 * t,
-                         acc[mi][ni][2 * hh], acc[mi][ni][2 * hh + 1], (int)blockIdx.z);
+        for (int j = 0; j < 16; ++j) v[j] = nkb > 0 ? __uint_as_float(r[j]) : 0.0f;
+        if (ok) op.store16(row, n0 + c0, v, (int)blockIdx.z);
+    }
+    if (!ok && lane == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                     "n"(TC)
+                     : "memory");
 }
 
-template <class Op>
-cudaError_t launch_gemm(const Op& op, long long kchunk, int splits, cudaStream_t s) {
-    const long long gm = (op.M() + BM - 1) / BM;
+template <class Op, int BN>
+cudaError_t launch_umma_bn(const Op& op, long long kchunk, int splits, int* err,
+                           cudaStream_t s) {
+    constexpr size_t smem = umma_smem<BN>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(umma_gemm_kernel<Op, BN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const long long gm = (op.M() + UM - 1) / UM;
     const int gn = (op.N() + BN - 1) / BN;
     if (gm > 0x7fffffffLL) return cudaErrorInvalidValue;
-    gemm_kernel<Op><<<dim3((unsigned)gm, gn, splits), kGemmThreads, 0, s>>>(op, kchunk);
+    umma_gemm_kernel<Op, BN><<<dim3((unsigned)gm, gn, splits), kGemmThreads, smem, s>>>(op, kchunk,
+                                                                                        err);
     return cudaGetLastError();
+}
+
+// The tile width: the smallest UMMA N (16, 32, 64, 128, 256) that covers N,
+// 256 above.
+template <class Op>
+cudaError_t launch_gemm(const Op& op, long long kchunk, int splits, int* err, cudaStream_t s) {
+    const int n = op.N();
+    if (n <= 16) return launch_umma_bn<Op, 16>(op, kchunk, splits, err, s);
+    if (n <= 32) return launch_umma_bn<Op, 32>(op, kchunk, splits, err, s);
+    if (n <= 64) return launch_umma_bn<Op, 64>(op, kchunk, splits, err, s);
+    if (n <= 128) return launch_umma_bn<Op, 128>(op, kchunk, splits, err, s);
+    return launch_umma_bn<Op, 256>(op, kchunk, splits, err, s);
 }
 
 // ---- elementwise and reduction kernels ----
@@ -610,6 +752,7 @@ struct lbm_nn {
     float* gout = nullptr;     // the loss gradient of yout [P][3]
     float* tmp3 = nullptr;     // the output stage's intermediate [P][3]
     double* ssum = nullptr;    // per instance: the staggered sums and fluid count
+    int* gemm_err = nullptr;   // set by a GEMM whose bounded wait ran out
     long long adam_t = 0;
     int64_t launches = 0;
     char err[512] = {0};
@@ -759,7 +902,7 @@ lbm_status forward(lbm_nn* nn, int n) {
             f.cin = c.cinp;
             f.cout = c.coutp;
             f.relu = c.relu;
-            e = launch_gemm(f, f.K(), 1, s);
+            e = launch_gemm(f, f.K(), 1, nn->gemm_err, s);
         } else if (op.k == lbm_nn::POOL) {
             const lbm_nn::Tensor& X = nn->t[op.a];
             pool_kernel<<<grid_of(pixels(nn, op.out, n) * X.cp), kThreads, 0, s>>>(
@@ -844,7 +987,7 @@ lbm_status backward(lbm_nn* nn, int n, float* loss) {
             wg.part = nn->part;
             wg.cin = c.cinp;
             wg.cout = c.coutp;
-            if ((e = launch_gemm(wg, kSplitPixels, splits, s)) != cudaSuccess) break;
+            if ((e = launch_gemm(wg, kSplitPixels, splits, nn->gemm_err, s)) != cudaSuccess) break;
             const long long nw = (long long)conv_wsize(c);
             split_sum_kernel<<<grid_of(nw), kThreads, 0, s>>>(nn->part, c.gw, splits, nw);
             if ((e = cudaGetLastError()) != cudaSuccess) break;
@@ -859,7 +1002,7 @@ lbm_status backward(lbm_nn* nn, int n, float* loss) {
                 dg.gin = G[c.in];
                 dg.cin = c.cinp;
                 dg.cout = c.coutp;
-                if ((e = launch_gemm(dg, dg.K(), 1, s)) != cudaSuccess) break;
+                if ((e = launch_gemm(dg, dg.K(), 1, nn->gemm_err, s)) != cudaSuccess) break;
                 ++nn->launches;
             }
         } else if (op.k == lbm_nn::POOL) {
@@ -890,6 +1033,19 @@ lbm_status backward(lbm_nn* nn, int n, float* loss) {
         "cudaMemcpyAsync(D2H)");
     NCK(nn, cudaStreamSynchronize(s), "cudaStreamSynchronize");
     if (loss) *loss = (float)(l * (double)inv_cnt);
+    return LBM_OK;
+}
+
+// After a synchronisation: a GEMM whose bounded wait ran out leaves its word
+// set (its tile was not stored).
+lbm_status check_gemm(lbm_nn* nn) {
+    int e = 0;
+    NCK(nn, cudaMemcpy(&e, nn->gemm_err, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy(D2H)");
+    if (e) {
+        NCK(nn, cudaMemset(nn->gemm_err, 0, sizeof(int)), "cudaMemset");
+        nn_err(nn, "a tensor-core GEMM gave up waiting for its MMAs");
+        return LBM_ERR_TIMEOUT;
+    }
     return LBM_OK;
 }
 
@@ -1013,6 +1169,8 @@ lbm_status lbm_nn_create(int levels, const int* channels, int max_batch, int hei
     NCKC(lbm::dev_alloc(&nn->gout, Pmax * 3 * sizeof(float)), "cudaMalloc(output gradient)");
     NCKC(lbm::dev_alloc(&nn->tmp3, Pmax * 3 * sizeof(float)), "cudaMalloc(output stage)");
     NCKC(lbm::dev_alloc(&nn->ssum, (size_t)nn->nb * 3 * sizeof(double)), "cudaMalloc(output sums)");
+    NCKC(lbm::dev_alloc(&nn->gemm_err, sizeof(int)), "cudaMalloc(error word)");
+    NCKC(cudaMemsetAsync(nn->gemm_err, 0, sizeof(int), nn->stream), "cudaMemset");
 #undef NCKC
     // He-normal initial weights (host generator), zero biases
     std::vector<float> params(lbm_nn_param_count(nn));
@@ -1045,6 +1203,7 @@ void lbm_nn_destroy(lbm_nn* nn) {
     cudaFree(nn->gout);
     cudaFree(nn->tmp3);
     cudaFree(nn->ssum);
+    cudaFree(nn->gemm_err);
     delete nn;
 }
 
@@ -1133,7 +1292,7 @@ lbm_status lbm_nn_forward(lbm_nn* nn, const float* x, int n, float* y) {
                             nn->stream),
         "cudaMemcpyAsync(D2H)");
     NCK(nn, cudaStreamSynchronize(nn->stream), "cudaStreamSynchronize");
-    return LBM_OK;
+    return check_gemm(nn);
 }
 
 lbm_status lbm_nn_gradients(lbm_nn* nn, const float* x, const float* target,
@@ -1143,6 +1302,7 @@ lbm_status lbm_nn_gradients(lbm_nn* nn, const float* x, const float* target,
     lbm_status s = upload_inputs(nn, x, target, fluid, n);
     if (s == LBM_OK) s = forward(nn, n);
     if (s == LBM_OK) s = backward(nn, n, loss);
+    if (s == LBM_OK) s = check_gemm(nn);
     if (s == LBM_OK && grads) s = transfer_params(nn, grads, false, true);
     return s;
 }
@@ -1176,7 +1336,7 @@ lbm_status lbm_nn_train_step(lbm_nn* nn, const float* x, const float* target,
     s = sync_weights(nn);
     if (s != LBM_OK) return s;
     NCK(nn, cudaStreamSynchronize(nn->stream), "cudaStreamSynchronize");
-    return LBM_OK;
+    return check_gemm(nn);
 }
 
 int64_t lbm_nn_launch_count(const lbm_nn* nn) { return nn ? nn->launches : -1; }
