@@ -40,16 +40,48 @@ using bf16 = __nv_bfloat16;
 constexpr int kThreads = 256;
 constexpr int kSplitPixels = 4096;  // pixels per block of the weight-gradient GEMM
 
-struct Geo {
-    int n, h, w;          // batch and grid
-    long long P;          // pixels n h w
+// Division by a divisor fixed at launch, for dividends in [0, 2^31):
+// q = (n m) >> s with m = ceil(2^s / d), s = 31 + ceil(log2 d) (exact in that
+// range: the error of m / 2^s is below 2^-31 / d).
+struct FastDiv {
+    unsigned d = 1;
+    unsigned long long m = 1ull << 31;
+    int s = 31;
+    FastDiv() = default;
+    explicit FastDiv(unsigned dv) : d(dv) {
+        int l = 0;
+        while ((1ull << l) < dv) ++l;
+        s = 31 + l;
+        m = ((1ull << s) + dv - 1) / dv;
+    }
+    __device__ __forceinline__ unsigned div(unsigned n) const {
+        return (unsigned)(((unsigned long long)n * m) >> s);
+    }
 };
 
+struct Geo {
+    int n, h, w;          // batch and grid
+    long long P;          // pixels n h w (below 2^31: checked at creation)
+    FastDiv fhw, fw;      // by h w and by w
+};
+
+Geo make_geo(int n, int h, int w, long long P) {
+    Geo g;
+    g.n = n;
+    g.h = h;
+    g.w = w;
+    g.P = P;
+    g.fhw = FastDiv((unsigned)(h * w));
+    g.fw = FastDiv((unsigned)w);
+    return g;
+}
+
 __device__ __forceinline__ bool shifted(const Geo& g, long long p, int dy, int dx, long long& q) {
-    const int hw = g.h * g.w;
-    const int nn = (int)(p / hw);
-    const int rem = (int)(p - (long long)nn * hw);
-    const int y = rem / g.w + dy, x = rem % g.w + dx;
+    const unsigned pp = (unsigned)p;
+    const unsigned nn = g.fhw.div(pp);
+    const unsigned rem = pp - nn * g.fhw.d;
+    const unsigned yy = g.fw.div(rem);
+    const int y = (int)yy + dy, x = (int)(rem - yy * g.fw.d) + dx;
     if (y < 0 || y >= g.h || x < 0 || x >= g.w) return false;
     q = ((long long)nn * g.h + y) * g.w + x;
     return true;
@@ -57,33 +89,41 @@ __device__ __forceinline__ bool shifted(const Geo& g, long long p, int dy, int d
 
 // ---- operand tiles of the tensor-core GEMM ----
 //
-// A tile holds rows r (of UM = 128 for A, BN for B) and the K chunk
-// [k0, k0 + UK) in the no-swizzle K-major layout of the tensor core's shared
-// memory descriptors: 8 x 8 core matrices of 8 rows by 16 bytes, stored
-// contiguously (128 bytes), the core matrices of one row group adjacent along
-// K (leading byte offset 128) and the row groups 8 core matrices apart
-// (stride byte offset 1024).
+// A tile holds rows r (UM = 128 of A, BN of B) and the K chunk [k0, k0 + UK)
+// in the tensor core's no-swizzle core-matrix layout: core matrices of
+// 8 x 16 bytes stored contiguously (128 bytes), the core matrices of one
+// group of 8 rows adjacent along K (leading byte offset 128) and the row
+// groups 8 core matrices apart (stride byte offset 1024).  K-major: a core
+// matrix row is 8 consecutive k of one row; MN-major: 8 consecutive rows at
+// one k.  Every operand arrives in 16-byte pieces of one of those two kinds,
+// copied by cp.async (zero-filled outside the operand).
 constexpr int UM = 128, UK = 64, kGemmThreads = 128;
 constexpr unsigned kLBO = 128, kSBO = (UK / 8) * 128;
 
-__device__ __forceinline__ unsigned tile_off(int r, int kc) {
-    return (unsigned)(r >> 3) * kSBO + (unsigned)(kc >> 3) * kLBO + (unsigned)(r & 7) * 16 +
-           (unsigned)(kc & 7) * 2;
+// byte offset of the 16-byte piece holding rows r .. r+7 at k (MN-major) or
+// row r at k .. k+7 (K-major), within a tile
+__device__ __forceinline__ unsigned kmajor_off(int r, int kc) {
+    return (unsigned)(r >> 3) * kSBO + (unsigned)(kc >> 3) * kLBO + (unsigned)(r & 7) * 16;
 }
-__device__ __forceinline__ void put8(unsigned char* t, int r, int kc, uint4 v) {
-    *reinterpret_cast<uint4*>(t + tile_off(r, kc)) = v;
+__device__ __forceinline__ unsigned mnmajor_off(int r8, int kc) {
+    return (unsigned)(r8 >> 3) * kSBO + (unsigned)(kc >> 3) * kLBO + (unsigned)(kc & 7) * 16;
 }
-// eight values along the rows r .. r+7 at one k (a transposed gather)
-__device__ __forceinline__ void put8_rows(unsigned char* t, int r, int kc, uint4 v) {
-    const bf16* e = reinterpret_cast<const bf16*>(&v);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) *reinterpret_cast<bf16*>(t + tile_off(r + j, kc)) = e[j];
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+// 16 bytes global -> shared, or 16 zero bytes when !valid
+__device__ __forceinline__ void cp16(unsigned dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
 }
 
 // Forward: out = act(conv(in) + b).  M = pixels, N = cout, K = 9 cin:
-// A[p][(tap, ci)] = in(p + s(tap))[ci], B[co][(tap, ci)] = W.
+// A[p][(tap, ci)] = in(p + s(tap))[ci], B[co][(tap, ci)] = W; both K-major.
 struct FwdOp {
+    static constexpr bool kAmn = false, kBmn = false;
     Geo g;
+    FastDiv fk;        // by cin (the K index's channel count)
     const bf16* in;    // [P][cin]
     const bf16* wf;    // [cout][9 cin]
     const float* bias; // [cout]
@@ -92,31 +132,31 @@ struct FwdOp {
     __host__ __device__ long long M() const { return g.P; }
     __host__ __device__ int N() const { return cout; }
     __host__ __device__ long long K() const { return 9LL * cin; }
-    __device__ void load_a(unsigned char* t, long long m0, long long k0, long long kend,
-                           int tid) const {
+    __device__ void load_a(unsigned t, long long m0, long long k0, long long kend, int tid) const {
 #pragma unroll
         for (int i = 0; i < UM * UK / 8 / kGemmThreads; ++i) {
             const int v = tid + i * kGemmThreads, r = v >> 3, kc = (v & 7) * 8;
             const long long p = m0 + r, k = k0 + kc;
-            uint4 val = make_uint4(0, 0, 0, 0);
+            const bf16* src = in;
+            bool ok = false;
             if (p < g.P && k < kend) {
-                const int tap = (int)(k / cin), ci = (int)(k - (long long)tap * cin);
+                const int tap = (int)fk.div((unsigned)k), ci = (int)k - tap * cin;
                 long long q;
-                if (shifted(g, p, tap / 3 - 1, tap % 3 - 1, q))
-                    val = *reinterpret_cast<const uint4*>(in + q * cin + ci);
+                if (shifted(g, p, tap / 3 - 1, tap % 3 - 1, q)) {
+                    src = in + q * cin + ci;
+                    ok = true;
+                }
             }
-            put8(t, r, kc, val);
+            cp16(t + kmajor_off(r, kc), src, ok);
         }
     }
-    __device__ void load_b(unsigned char* t, int n0, long long k0, long long kend, int tid,
+    __device__ void load_b(unsigned t, int n0, long long k0, long long kend, int tid,
                            int bn) const {
         for (int v = tid; v < bn * (UK / 8); v += kGemmThreads) {
             const int r = v >> 3, kc = (v & 7) * 8;
             const long long k = k0 + kc;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (n0 + r < cout && k < kend)
-                val = *reinterpret_cast<const uint4*>(wf + (long long)(n0 + r) * K() + k);
-            put8(t, r, kc, val);
+            const bool ok = n0 + r < cout && k < kend;
+            cp16(t + kmajor_off(r, kc), ok ? wf + (long long)(n0 + r) * K() + k : wf, ok);
         }
     }
     __device__ void store16(long long row, int col0, const float* v, int) const {
@@ -137,9 +177,11 @@ struct FwdOp {
 };
 
 // Input gradient: gin = conv^T(gpre).  M = pixels, N = cin, K = 9 cout:
-// A[q][(tap, co)] = g(q - s(tap))[co], B[ci][(tap, co)] = W.
+// A[q][(tap, co)] = g(q - s(tap))[co], B[ci][(tap, co)] = W; both K-major.
 struct DgradOp {
+    static constexpr bool kAmn = false, kBmn = false;
     Geo g;
+    FastDiv fk;        // by cout
     const bf16* gpre;  // [P][cout]
     const bf16* wd;    // [cin][9 cout]
     bf16* gin;         // [P][cin]
@@ -147,31 +189,31 @@ struct DgradOp {
     __host__ __device__ long long M() const { return g.P; }
     __host__ __device__ int N() const { return cin; }
     __host__ __device__ long long K() const { return 9LL * cout; }
-    __device__ void load_a(unsigned char* t, long long m0, long long k0, long long kend,
-                           int tid) const {
+    __device__ void load_a(unsigned t, long long m0, long long k0, long long kend, int tid) const {
 #pragma unroll
         for (int i = 0; i < UM * UK / 8 / kGemmThreads; ++i) {
             const int v = tid + i * kGemmThreads, r = v >> 3, kc = (v & 7) * 8;
             const long long p = m0 + r, k = k0 + kc;
-            uint4 val = make_uint4(0, 0, 0, 0);
+            const bf16* src = gpre;
+            bool ok = false;
             if (p < g.P && k < kend) {
-                const int tap = (int)(k / cout), co = (int)(k - (long long)tap * cout);
+                const int tap = (int)fk.div((unsigned)k), co = (int)k - tap * cout;
                 long long q;
-                if (shifted(g, p, 1 - tap / 3, 1 - tap % 3, q))
-                    val = *reinterpret_cast<const uint4*>(gpre + q * cout + co);
+                if (shifted(g, p, 1 - tap / 3, 1 - tap % 3, q)) {
+                    src = gpre + q * cout + co;
+                    ok = true;
+                }
             }
-            put8(t, r, kc, val);
+            cp16(t + kmajor_off(r, kc), src, ok);
         }
     }
-    __device__ void load_b(unsigned char* t, int n0, long long k0, long long kend, int tid,
+    __device__ void load_b(unsigned t, int n0, long long k0, long long kend, int tid,
                            int bn) const {
         for (int v = tid; v < bn * (UK / 8); v += kGemmThreads) {
             const int r = v >> 3, kc = (v & 7) * 8;
             const long long k = k0 + kc;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (n0 + r < cin && k < kend)
-                val = *reinterpret_cast<const uint4*>(wd + (long long)(n0 + r) * K() + k);
-            put8(t, r, kc, val);
+            const bool ok = n0 + r < cin && k < kend;
+            cp16(t + kmajor_off(r, kc), ok ? wd + (long long)(n0 + r) * K() + k : wd, ok);
         }
     }
     __device__ void store16(long long row, int col0, const float* v, int) const {
@@ -189,10 +231,13 @@ struct DgradOp {
 // Weight gradient, transposed so that the taps and input channels (9 cin,
 // usually the larger side) fill the 128 rows: M = 9 cin, N = cout,
 // K = pixels (one split of them per blockIdx.z):
-// A[(tap, ci)][p] = in(p + s(tap))[ci], B[co][p] = g(p)[co];
+// A[(tap, ci)][p] = in(p + s(tap))[ci], B[co][p] = g(p)[co], both MN-major
+// (8 consecutive channels of one pixel are one 16-byte piece);
 // part[z][co][(tap, ci)] = D[(tap, ci)][co].
 struct WgradOp {
+    static constexpr bool kAmn = true, kBmn = true;
     Geo g;
+    FastDiv fk;        // by cin
     const bf16* gpre;  // [P][cout]
     const bf16* in;    // [P][cin]
     float* part;       // [splits][cout][9 cin]
@@ -200,34 +245,34 @@ struct WgradOp {
     __host__ __device__ long long M() const { return 9LL * cin; }
     __host__ __device__ int N() const { return cout; }
     __host__ __device__ long long K() const { return g.P; }
-    __device__ void load_a(unsigned char* t, long long m0, long long k0, long long kend,
-                           int tid) const {
-        // items (row group of 8 channels, pixel): 16 x 64, consecutive
-        // threads on consecutive channel groups of one pixel
+    __device__ void load_a(unsigned t, long long m0, long long k0, long long kend, int tid) const {
+        // pieces (group of 8 rows, pixel): 16 x 64, consecutive threads on
+        // consecutive channel groups of one pixel
 #pragma unroll
         for (int i = 0; i < UM * UK / 8 / kGemmThreads; ++i) {
             const int v = tid + i * kGemmThreads, grp = v & 15, kk = v >> 4;
             const long long m = m0 + grp * 8, p = k0 + kk;
-            uint4 val = make_uint4(0, 0, 0, 0);
+            const bf16* src = in;
+            bool ok = false;
             if (m < M() && p < kend) {
-                const int tap = (int)(m / cin), ci = (int)(m - (long long)tap * cin);
+                const int tap = (int)fk.div((unsigned)m), ci = (int)m - tap * cin;
                 long long q;
-                if (shifted(g, p, tap / 3 - 1, tap % 3 - 1, q))
-                    val = *reinterpret_cast<const uint4*>(in + q * cin + ci);
+                if (shifted(g, p, tap / 3 - 1, tap % 3 - 1, q)) {
+                    src = in + q * cin + ci;
+                    ok = true;
+                }
             }
-            put8_rows(t, grp * 8, kk, val);
+            cp16(t + mnmajor_off(grp * 8, kk), src, ok);
         }
     }
-    __device__ void load_b(unsigned char* t, int n0, long long k0, long long kend, int tid,
+    __device__ void load_b(unsigned t, int n0, long long k0, long long kend, int tid,
                            int bn) const {
         for (int v = tid; v < (bn / 8) * UK; v += kGemmThreads) {
             const int grp = v % (bn / 8), kk = v / (bn / 8);
             const int co = n0 + grp * 8;
             const long long p = k0 + kk;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (co < cout && p < kend)
-                val = *reinterpret_cast<const uint4*>(gpre + p * cout + co);
-            put8_rows(t, grp * 8, kk, val);
+            const bool ok = co < cout && p < kend;
+            cp16(t + mnmajor_off(grp * 8, kk), ok ? gpre + p * cout + co : gpre, ok);
         }
     }
     __device__ void store16(long long row, int col0, const float* v, int z) const {
@@ -243,9 +288,6 @@ struct WgradOp {
 
 // ---- the tensor-core GEMM: tcgen05.mma, accumulator in tensor memory ----
 
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
 // shared memory matrix descriptor: start address, leading / stride byte
 // offsets (all >> 4), version 1 at bits 46-47, no swizzle
 __device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
@@ -266,38 +308,46 @@ __device__ __forceinline__ bool mbar_wait_parity(unsigned bar, unsigned parity) 
     }
     return false;
 }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int BN>
 __host__ __device__ constexpr int tmem_cols() { return BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256; }
+// pipeline depth: four stages up to 64 columns, three above (two CTAs per
+// SM up to 128 columns)
 template <int BN>
-constexpr size_t umma_smem() { return 2 * (size_t)(UM + BN) * UK * 2 + 64; }
+__host__ __device__ constexpr int gemm_stages() { return BN <= 64 ? 4 : 3; }
+template <int BN>
+constexpr size_t umma_smem() { return (size_t)gemm_stages<BN>() * (UM + BN) * UK * 2 + 128; }
 
-// One CTA computes a UM x BN tile of D = A B^T over its K range: K chunks of
-// UK in two shared-memory buffers, four MMAs of K = 16 per chunk issued by
-// one thread and committed to the buffer's mbarrier, so that the threads
-// gather the next chunk while the tensor core works; the accumulator lives in
-// BN columns of tensor memory and is read back by each warp for its 32 rows.
-// Every wait is bounded; one that runs out sets *err and the tile is not
-// stored.
+// One CTA computes a UM x BN tile of D = A B^T over its K range, in chunks of
+// UK: the threads keep NS - 1 chunks in flight as cp.async groups, one
+// thread issues the four MMAs (K = 16 each) of a landed chunk and commits
+// them to its stage's mbarrier, which frees the stage for the chunk NS - 1
+// ahead.  The accumulator lives in BN columns of tensor memory; each warp
+// reads its 32 rows back.  Every wait is bounded; one that runs out sets
+// *err and the tile is not stored.
 template <class Op, int BN>
 __global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const Op op, long long kchunk,
                                                                  int* err) {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
-    extern __shared__ __align__(1024) unsigned char sm[];
-    // buffer b: A at sm + b UM UK 2, B at sm + 2 UM UK 2 + b BN UK 2
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * (UM + BN) * UK * 2);
-    unsigned* tslot = reinterpret_cast<unsigned*>(bars + 2);
+    constexpr int NS = gemm_stages<BN>();
     constexpr int TC = tmem_cols<BN>();
+    constexpr unsigned kStage = (UM + BN) * UK * 2;  // A then B of one stage
+    extern __shared__ __align__(1024) unsigned char sm[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + NS * kStage);
+    unsigned* tslot = reinterpret_cast<unsigned*>(bars + NS);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long m0 = (long long)blockIdx.x * UM;
     const int n0 = blockIdx.y * BN;
     const long long kbeg = (long long)blockIdx.z * kchunk;
     const long long kend = min(op.K(), kbeg + kchunk);
     const int nkb = kend > kbeg ? (int)((kend - kbeg + UK - 1) / UK) : 0;
-    const unsigned bar0 = smem_addr(bars);
+    const unsigned s0 = smem_addr(sm), bar0 = smem_addr(bars);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        for (int s = 0; s < NS; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * s) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -311,24 +361,30 @@ __global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const Op op, lo
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned taddr = *tslot;
-    // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major
-    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                               ((uint32_t)(UM >> 4) << 24);
+    // instruction descriptor: FP32 accumulator, BF16 A and B, their majors
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                               ((Op::kAmn ? 1u : 0u) << 15) | ((Op::kBmn ? 1u : 0u) << 16) |
+                               ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+    auto load = [&](int kb) {
+        const unsigned st = s0 + (unsigned)(kb % NS) * kStage;
+        const long long k0 = kbeg + (long long)kb * UK;
+        op.load_a(st, m0, k0, kend, tid);
+        op.load_b(st + UM * UK * 2, n0, k0, kend, tid, BN);
+    };
+#pragma unroll
+    for (int kb = 0; kb < NS - 1; ++kb) {
+        if (kb < nkb) load(kb);
+        cp_commit();
+    }
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
-        const int b = kb & 1;
-        // the MMAs of chunk kb - 2 read this buffer
-        if (kb >= 2) ok &= mbar_wait_parity(bar0 + 8u * b, (unsigned)(((kb - 2) >> 1) & 1));
-        const long long k0 = kbeg + (long long)kb * UK;
-        unsigned char* At = sm + b * (UM * UK * 2);
-        unsigned char* Bt = sm + 2 * UM * UK * 2 + b * (BN * UK * 2);
-        op.load_a(At, m0, k0, kend, tid);
-        op.load_b(Bt, n0, k0, kend, tid, BN);
+        const int st = kb % NS;
+        cp_wait<NS - 2>();  // this thread's pieces of chunk kb have landed
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+        __syncthreads();    // everyone's have
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned a0 = smem_addr(At), b0 = smem_addr(Bt);
+            const unsigned a0 = s0 + (unsigned)st * kStage, b0 = a0 + UM * UK * 2;
 #pragma unroll
             for (int kk = 0; kk < UK / 16; ++kk) {
                 const uint64_t ad = smem_desc(a0 + kk * 2 * kLBO, kLBO, kSBO);
@@ -342,13 +398,25 @@ __global__ void __launch_bounds__(kGemmThreads) umma_gemm_kernel(const Op op, lo
             }
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    bar0 + 8u * b)
+                    bar0 + 8u * st)
                 : "memory");
         }
+        // the chunk NS - 1 ahead goes into the stage of chunk kb - 1, once
+        // the MMAs that read it are done
+        const int nk = kb + NS - 1;
+        if (nk < nkb) {
+            if (kb >= 1) {
+                const int ps = (kb - 1) % NS;
+                ok &= mbar_wait_parity(bar0 + 8u * ps, (unsigned)(((kb - 1) / NS) & 1));
+            }
+            load(nk);
+        }
+        cp_commit();
     }
     // the last commit tracks every MMA of the tile
     if (nkb > 0)
-        ok &= mbar_wait_parity(bar0 + 8u * ((nkb - 1) & 1), (unsigned)(((nkb - 1) >> 1) & 1));
+        ok &= mbar_wait_parity(bar0 + 8u * ((nkb - 1) % NS), (unsigned)(((nkb - 1) / NS) & 1));
+    cp_wait<0>();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const long long row = m0 + 32 * warp + lane;
 #pragma unroll 1
@@ -398,13 +466,16 @@ cudaError_t launch_umma_bn(const Op& op, long long kchunk, int splits, int* err,
 
 // The tile width: the smallest UMMA N (16, 32, 64, 128, 256) that covers N,
 // 256 above.
+#ifndef LBM_GEMM_WIDE
+#define LBM_GEMM_WIDE 1
+#endif
 template <class Op>
 cudaError_t launch_gemm(const Op& op, long long kchunk, int splits, int* err, cudaStream_t s) {
     const int n = op.N();
     if (n <= 16) return launch_umma_bn<Op, 16>(op, kchunk, splits, err, s);
     if (n <= 32) return launch_umma_bn<Op, 32>(op, kchunk, splits, err, s);
     if (n <= 64) return launch_umma_bn<Op, 64>(op, kchunk, splits, err, s);
-    if (n <= 128) return launch_umma_bn<Op, 128>(op, kchunk, splits, err, s);
+    if (n <= 128 || !LBM_GEMM_WIDE) return launch_umma_bn<Op, 128>(op, kchunk, splits, err, s);
     return launch_umma_bn<Op, 256>(op, kchunk, splits, err, s);
 }
 
@@ -894,7 +965,8 @@ lbm_status forward(lbm_nn* nn, int n) {
             const lbm_nn::Conv& c = nn->conv[op.a];
             const lbm_nn::Tensor& X = nn->t[c.in];
             FwdOp f;
-            f.g = Geo{n, X.h, X.w, pixels(nn, c.in, n)};
+            f.g = make_geo(n, X.h, X.w, pixels(nn, c.in, n));
+            f.fk = FastDiv((unsigned)c.cinp);
             f.in = X.v;
             f.wf = c.wf;
             f.bias = c.bm;
@@ -981,7 +1053,8 @@ lbm_status backward(lbm_nn* nn, int n, float* loss) {
             // weight gradient, split over pixels
             const int splits = (int)((Pc + kSplitPixels - 1) / kSplitPixels);
             WgradOp wg;
-            wg.g = Geo{n, X.h, X.w, Pc};
+            wg.g = make_geo(n, X.h, X.w, Pc);
+            wg.fk = FastDiv((unsigned)c.cinp);
             wg.gpre = gpre;
             wg.in = X.v;
             wg.part = nn->part;
@@ -997,6 +1070,7 @@ lbm_status backward(lbm_nn* nn, int n, float* loss) {
             if (c.in != nn->x_id) {
                 DgradOp dg;
                 dg.g = wg.g;
+                dg.fk = FastDiv((unsigned)c.coutp);
                 dg.gpre = gpre;
                 dg.wd = c.wd;
                 dg.gin = G[c.in];
