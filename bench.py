@@ -70,6 +70,11 @@ def parse():
                     help="skip the learned warm-start measurement")
     ap.add_argument("--warm-train", type=int, default=1024)
     ap.add_argument("--warm-epochs", type=int, default=60)
+    ap.add_argument("--nn-only", action="store_true",
+                    help="only the surrogate's forward and training-step times")
+    ap.add_argument("--nn-prof", action="store_true",
+                    help="with --nn-only: two forward passes of a one-level 256-channel "
+                         "network on 16 instances of 64 x 64 (a case for ncu)")
     ap.add_argument("--config4-ttr", action="store_true",
                     help="only the time to R <= 1e-8 of the full 512-lattice sweep under a "
                          "step cap, batched against sequential (minutes)")
@@ -444,6 +449,45 @@ def config4_time_to_residual(torch, count=512, cap=20000, tol=1e-8, check=100):
                               for k in range(count) if not (conv_b[k] and conv_s[k])]}
 
 
+def surrogate_times(prof_only=False):
+    """Wall time of the surrogate's forward pass and of one Adam training step
+    (synchronous calls through the C ABI, host inputs) for the warm-start
+    network and a one-level 256-channel network, 16 instances of 64 x 64."""
+    import numpy as np
+    from paper_2103_02119_gb300 import lbm as L
+    rng = np.random.default_rng(0)
+    if prof_only:
+        nn = L.lbm_nn_create([256], 16, 64, 64, seed=0)
+        x = rng.standard_normal((16, 64, 64, 4)).astype(np.float32)
+        L.lbm_nn_forward(nn, x)
+        L.lbm_nn_forward(nn, x)
+        L.lbm_nn_destroy(nn)
+        return {"prof": "two forward passes of [256] at 16 x 64 x 64"}
+    out = {}
+    for channels in ([32, 64, 128, 256], [256]):
+        n, hw = 16, 64
+        nn = L.lbm_nn_create(channels, n, hw, hw, seed=0)
+        x = rng.standard_normal((n, hw, hw, 4)).astype(np.float32)
+        x[..., 0] = rng.random((n, hw, hw)) > 0.9
+        t = rng.standard_normal((n, hw, hw, 3)).astype(np.float32)
+        fl = (x[..., 0] < 0.5).astype(np.uint8)
+        for _ in range(3):
+            L.lbm_nn_forward(nn, x)
+            L.lbm_nn_train_step(nn, x, t, fl, 1e-4)
+        t0 = time.perf_counter()
+        for _ in range(20):
+            L.lbm_nn_forward(nn, x)
+        tf = (time.perf_counter() - t0) / 20
+        t0 = time.perf_counter()
+        for _ in range(20):
+            L.lbm_nn_train_step(nn, x, t, fl, 1e-4)
+        tt = (time.perf_counter() - t0) / 20
+        out[str(channels)] = {"instances": f"{n} x {hw} x {hw}", "forward_ms": tf * 1e3,
+                              "train_step_ms": tt * 1e3}
+        L.lbm_nn_destroy(nn)
+    return out
+
+
 # ------------------------------------------------------------ small lattice --
 
 def small_lattice(torch):
@@ -505,7 +549,7 @@ def warm_start_measure(torch, ntrain, epochs, n=32, ntest=32):
     ws.close()
     return {"instances": f"{n}x{n} lid-driven cavities with obstacles, a in [0.5, 1], "
                          "Re in [20, 200], seeded; train seed 0, test seed 1",
-            "network": "4-level conv encoder-decoder, 32-256 channels, BF16 mma.sync",
+            "network": "4-level conv encoder-decoder, 32-256 channels, BF16 tcgen05 (TMEM accumulator)",
             "train_instances": len(wls), "epochs": epochs, "final_train_loss": hist[-1],
             "test_instances": ntest, "test_rms_error": rms,
             "data_seconds": t_data, "train_seconds": t_train,
@@ -591,6 +635,10 @@ def main():
             shape = tuple(int(v) for v in args.batch_shape.split(",")) if args.batch_shape else None
             print(json.dumps(batch_throughput(torch, args.batch_count, args.batch_steps, shape)),
                   flush=True)
+        return
+    if args.nn_only:
+        if rank == 0:
+            print(json.dumps(surrogate_times(args.nn_prof)), flush=True)
         return
     if args.config4_ttr:
         if rank == 0:
