@@ -492,21 +492,26 @@ def surrogate_times(prof_only=False):
 
 def small_lattice(torch):
     """Config 1 (Poiseuille channel, 32 x 32, a = 0.5, FP64, 5,000 steps):
-    a lattice this small is bound by launch latency; lbm_step replays runs
-    of 50 steps from a CUDA graph, against one call per step."""
+    a lattice this small is bound by latency.  By default lbm_step runs it on
+    the cluster kernel (up to 1024 steps per launch); against it, the
+    row-band kernel with runs of 50 steps replayed from a CUDA graph, and
+    with one call per step."""
+    from paper_2103_02119_gb300 import lbm
     from paper_2103_02119_gb300 import workloads as W
     from paper_2103_02119_gb300.lbm import Lattice
     stream = torch.cuda.current_stream()
     wl = W.poiseuille(ny=32, nx=32, a=0.5, cs2=0.16, nu=0.1, U=0.01)
     out = {"workload": "Poiseuille channel 32x32, a=0.5, nu=0.1, FP64", "steps": 5000}
-    for mode in ("graph", "per_call"):
+    for mode in ("cluster", "graph", "per_call"):
         lat = Lattice.from_workload(wl, precision=64, stream=stream)
+        if mode != "cluster":
+            lbm.lbm_set_small_path(lat.h, False)
         lat.step(100)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        if mode == "graph":
+        if mode != "per_call":
             lat.step(5000)
         else:
             for _ in range(5000):

@@ -124,7 +124,7 @@ lbm_status lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
 /* Advance nsteps >= 0 time steps (collide + stream, Sec. 4), one kernel
  * launch per step; runs of 50 steps replay a CUDA graph the handle captures
  * once per starting buffer (on a stream of its own; lbm_set_force drops
- * it).  Asynchronous: the return value reports launch errors only. */
+ * it).  Small lattices run many steps per launch (lbm_set_small_path).  Asynchronous: the return value reports launch errors only. */
 lbm_status lbm_step(lbm_handle* h, int64_t nsteps);
 
 /* Replace the uniform body force density F (Sec. 4: it shifts the velocity
@@ -132,6 +132,18 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps);
  * source moments); takes effect from the next step.  Non-finite values give
  * LBM_ERR_INVALID. */
 lbm_status lbm_set_force(lbm_handle* h, double Fx, double Fy);
+
+/* Kernel choice for small lattices (library plumbing; the paper runs one
+ * fused step per launch at every size).  A lattice of at most 4096 cells
+ * whose cluster fits the device runs the steps of an lbm_step call in
+ * launches of up to 1024 steps each, every launch one thread-block cluster
+ * of min(ny, 16) CTAs that synchronise twice per step (density field, then
+ * collide and stream); the states are bit for bit those of the row-band
+ * kernel.  enable = 0 makes the handle use the row-band kernel (one launch
+ * per step); enable = 1 (the default where available) brings the cluster
+ * back.  enable not 0 or 1, or 1 for a lattice without the cluster path:
+ * LBM_ERR_INVALID. */
+lbm_status lbm_set_small_path(lbm_handle* h, int enable);
 
 /* Test hook for the failure path of the bounded waits (the paper has no
  * counterpart: this is library plumbing).  A step kernel waits for each row

@@ -62,6 +62,8 @@ struct lbm_handle {
     int diag_blocks = 0;
     int bx = 0, nbands = 0;
     int64_t steps = 0, launches = 0;
+    void* dfield = nullptr;    // small lattices: the density field of a step
+    bool small = false;        // steps run as one cluster launch (small_step.cu)
     cudaStream_t cap = nullptr;                     // owned, for graph capture only
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // runs of steps from f[0] / f[1]
     char err[512] = {0};
@@ -74,6 +76,8 @@ thread_local char g_err[512] = "no error";
 
 // Population layout of every handle (see lbm_device.cuh).
 constexpr bool kRowInterleaved = false;
+// steps per launch of the small-lattice kernel (bounds one launch to a few ms)
+constexpr int kSmallRun = 1024;
 
 void set_err(lbm_handle* h, const char* fmt, ...) {
     char* dst = h ? h->err : g_err;
@@ -396,6 +400,19 @@ lbm_status ensure_run_graph(lbm_handle* h, const KParams<T>& k, int from) {
 template <typename T>
 lbm_status step_lattice(lbm_handle* h, int64_t nsteps) {
     const KParams<T> k = kparams<T>(h);
+    if (h->small) {  // one cluster launch runs up to kSmallRun steps
+        for (int64_t left = nsteps; left > 0;) {
+            const int n = left < kSmallRun ? (int)left : kSmallRun;
+            CK(h, lbm::launch_small_run<T>((T*)h->f[0], (T*)h->f[1], (T*)h->dfield, k, h->cur, n,
+                                           h->stream),
+               "small-lattice step kernel");
+            h->cur ^= n & 1;
+            h->launches += 1;
+            h->steps += n;
+            left -= n;
+        }
+        return LBM_OK;
+    }
     int64_t left = nsteps;
     while (left >= kRunSteps) {
         if (lbm_status st = ensure_run_graph<T>(h, k, h->cur); st != LBM_OK) return st;
@@ -531,6 +548,16 @@ lbm_status lbm_create(const lbm_params* p, const uint8_t* solid_mask, void* cuda
     if (nb > p->ny) nb = p->ny;
     if (nb > 65535) nb = 65535;  // grid.y limit
     h->nbands = nb;
+    // small lattices: all the steps of an lbm_step call in one launch of one
+    // thread-block cluster, when the device can hold it
+    if (h->N <= lbm::kSmallCells && !kRowInterleaved) {
+        const bool fits = f64 ? lbm::small_run_fits<double>(kparams<double>(h))
+                              : lbm::small_run_fits<float>(kparams<float>(h));
+        if (fits) {
+            CKC(lbm::dev_alloc(&h->dfield, (size_t)h->N * elem_size(h)), "cudaMalloc(density field)");
+            h->small = true;
+        }
+    }
 #undef CKC
     lbm_status s = lbm_init_fields(h, nullptr, nullptr, nullptr, 0);
     if (s != LBM_OK) return fail(s);
@@ -545,6 +572,7 @@ void lbm_destroy(lbm_handle* h) {
     if (h->f[0]) cudaFree(h->f[0]);
     if (h->f[1]) cudaFree(h->f[1]);
     if (h->lmask) cudaFree(h->lmask);
+    if (h->dfield) cudaFree(h->dfield);
     if (h->uprev) cudaFree(h->uprev);
     if (h->stage) cudaFree(h->stage);
     if (h->part) cudaFree(h->part);
@@ -582,6 +610,21 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
         if (st != LBM_OK) return st;
         nsteps -= n;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_small_path(lbm_handle* h, int enable) {
+    if (!h) return LBM_ERR_INVALID;
+    if (enable != 0 && enable != 1) {
+        set_err(h, "enable must be 0 or 1");
+        return LBM_ERR_INVALID;
+    }
+    if (enable && !h->dfield) {
+        set_err(h, "this lattice has no small-lattice path (more than 4096 cells, or the cluster "
+                   "does not fit the device)");
+        return LBM_ERR_INVALID;
+    }
+    h->small = enable != 0;
     return LBM_OK;
 }
 

@@ -38,6 +38,18 @@ cudaError_t launch_step_free(const T* fin, T* fout, const KParams<T>& p, int bx,
                              cudaStream_t s);
 template <typename T>
 int step_occupancy(int bx, bool mask);
+
+// Small lattices (at most kSmallCells cells): nsteps steps in one launch of
+// one thread-block cluster of min(ny, kSmallCluster) CTAs, from buffer
+// `from` (f0 or f1); dfield: nx*ny values of T (the density field of a step).
+constexpr long long kSmallCells = 4096;
+constexpr int kSmallCluster = 16;
+template <typename T>
+cudaError_t launch_small_run(T* f0, T* f1, T* dfield, const KParams<T>& p, int from, int nsteps,
+                             cudaStream_t s);
+// whether such a cluster launch fits this device (queried, no launch)
+template <typename T>
+bool small_run_fits(const KParams<T>& p);
 // columns of lattice one block of bx threads of the step kernel covers
 template <typename T>
 int step_segment_width(int bx);

@@ -76,6 +76,7 @@ def _load():
     L.lbm_step.argtypes = [_P, ctypes.c_int64]
     L.lbm_set_force.argtypes = [_P, ctypes.c_double, ctypes.c_double]
     L.lbm_set_wait_limit.argtypes = [_P, ctypes.c_int64]
+    L.lbm_set_small_path.argtypes = [_P, ctypes.c_int]
     L.lbm_debug_fail_alloc.argtypes = [ctypes.c_int64]
     L.lbm_moments.argtypes = [_P, _P, _P, _P, ctypes.c_int]
     L.lbm_get_f.argtypes = [_P, _P, ctypes.c_int]
@@ -219,6 +220,10 @@ def lbm_step(h, nsteps: int):
 
 def lbm_set_force(h, Fx: float, Fy: float):
     _check(lib.lbm_set_force(h, float(Fx), float(Fy)), h)
+
+
+def lbm_set_small_path(h, enable: bool):
+    _check(lib.lbm_set_small_path(h, int(bool(enable))), h)
 
 
 def lbm_set_wait_limit(h, polls: int):

@@ -59,7 +59,8 @@ def test_parity(orc, name, precision):
     o.step(13)
     g.step(13)
     compare(o, g, precision)
-    assert g.step_count == 20 and g.launch_count == 20
+    # lattices of at most 4096 cells run each call's steps in one launch
+    assert g.step_count == 20 and g.launch_count == (2 if wl.nx * wl.ny <= 4096 else 20)
 
 
 @pytest.mark.parametrize("name", sorted(CONFIGS))
