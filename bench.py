@@ -69,6 +69,12 @@ def parse():
     ap.add_argument("--no-warm", action="store_true",
                     help="skip the learned warm-start measurement")
     ap.add_argument("--warm-train", type=int, default=1024)
+    ap.add_argument("--warm-n", type=int, default=32,
+                    help="cavity size n x n of the warm-start instances")
+    ap.add_argument("--warm-test", type=int, default=32,
+                    help="held-out warm-start instances")
+    ap.add_argument("--warm-only", action="store_true",
+                    help="print only the warm-start measurement")
     ap.add_argument("--warm-epochs", type=int, default=60)
     ap.add_argument("--nn-only", action="store_true",
                     help="only the surrogate's forward and training-step times")
@@ -548,10 +554,17 @@ def warm_start_measure(torch, ntrain, epochs, n=32, ntest=32):
     rest = WS.solve(test, stream=stream)
     warm = WS.solve(test, inits=[WS.fields_of(w, y[k]) for k, w in enumerate(test)],
                     stream=stream)
-    tt = np.stack([WS.targets_of(w, *rest["fields"][k]) for k, w in enumerate(test)])
+    tt = np.stack([WS.targets_of(w, *rest["mean_fields"][k]) for k, w in enumerate(test)])
     m = WS.fluid_of(test)[..., None].astype(bool)
     rms = float(np.sqrt(((y - tt) ** 2 * m).sum() / (3 * m.sum())))
     ws.close()
+    ok = [k for k in range(ntest) if 0.0 <= rest["residual"][k] <= 1e-8
+          and 0.0 <= warm["residual"][k] <= 1e-8]
+    # do the two starts end in the same steady state?  max |u_warm - u_rest|
+    # over the fluid, in units of the lid speed (two-step mean fields)
+    du = [max(float(np.abs(warm["mean_fields"][k][c] - rest["mean_fields"][k][c]).max())
+              for c in (1, 2)) / test[k].info["U"] for k in ok]
+    ratio = warm["steps"][ok] / np.maximum(rest["steps"][ok], 1)
     return {"instances": f"{n}x{n} lid-driven cavities with obstacles, a in [0.5, 1], "
                          "Re in [20, 200], seeded; train seed 0, test seed 1",
             "network": "4-level conv encoder-decoder, 32-256 channels, BF16 tcgen05 (TMEM accumulator)",
@@ -562,7 +575,11 @@ def warm_start_measure(torch, ntrain, epochs, n=32, ntest=32):
             "rest_steps_mean": float(rest["steps"].mean()),
             "warm_steps_mean": float(warm["steps"].mean()),
             "rest_seconds": rest["seconds"], "warm_seconds": warm["seconds"] + t_pred,
-            "steps_ratio_warm_over_rest": float(warm["steps"].mean() / rest["steps"].mean())}
+            "steps_ratio_warm_over_rest": float(warm["steps"].mean() / rest["steps"].mean()),
+            "both_converged": len(ok),
+            "per_instance_ratio_median": float(np.median(ratio)) if ok else None,
+            "warm_slower_instances": int((ratio > 1).sum()),
+            "max_du_over_U_warm_vs_rest": max(du) if du else None}
 
 
 # -------------------------------------------------------------- oracle arm --
@@ -640,6 +657,11 @@ def main():
             shape = tuple(int(v) for v in args.batch_shape.split(",")) if args.batch_shape else None
             print(json.dumps(batch_throughput(torch, args.batch_count, args.batch_steps, shape)),
                   flush=True)
+        return
+    if args.warm_only:
+        if rank == 0:
+            print(json.dumps(warm_start_measure(torch, args.warm_train, args.warm_epochs,
+                                                n=args.warm_n, ntest=args.warm_test)), flush=True)
         return
     if args.nn_only:
         if rank == 0:
@@ -736,7 +758,8 @@ def main():
 
     warm = None
     if rank == 0 and not args.no_warm:
-        warm = warm_start_measure(torch, args.warm_train, args.warm_epochs)
+        warm = warm_start_measure(torch, args.warm_train, args.warm_epochs, n=args.warm_n,
+                                  ntest=args.warm_test)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -54,7 +54,8 @@ typedef enum {
     LBM_ERR_TIMEOUT = -5,  /* a step kernel gave up waiting for its staged data
                               (reported by lbm_diagnostics; the state is not
                               valid after it)                                  */
-    LBM_ERR_STATE = -6     /* state buffer of the wrong size                   */
+    LBM_ERR_STATE = -6,    /* state buffer of the wrong size                   */
+    LBM_ERR_BOUNDS = -7    /* checked build: a device bounds check failed      */
 } lbm_status;
 
 /* Number of doubles written by lbm_diagnostics. */
@@ -93,6 +94,16 @@ typedef struct {
                               and bounce-back only, a test mode in which a
                               step is a permutation of the state)               */
 } lbm_params;
+
+/* Build flags of the loaded library (library plumbing): bit 0
+ * (LBM_BUILD_CHECKED) is set in the checked build, compiled with
+ * LBM_CHECKED, whose step kernels test every computed global, link-mask and
+ * shared-memory index; a failed test skips the access, and the next
+ * lbm_diagnostics, lbm_diagnostics_noalloc or lbm_batch_residuals returns
+ * LBM_ERR_BOUNDS (the state is then not valid).  The normal build has no
+ * such tests. */
+#define LBM_BUILD_CHECKED 1
+int lbm_build_flags(void);
 
 /* Fill *p with defaults: 64 x 64 periodic, a = 1, cs2 = 1/3 (the square
  * lattice, where the corrections of Eq. 23-24 vanish), all omega 1, no

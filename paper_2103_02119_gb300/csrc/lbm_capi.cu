@@ -13,6 +13,7 @@
 #include "dev_alloc.h"
 #include "lbm.h"
 #include "lbm_launch.h"
+#include "nvtx_range.h"
 
 using lbm::AuxParams;
 using lbm::CollConst;
@@ -430,6 +431,16 @@ lbm_status step_lattice(lbm_handle* h, int64_t nsteps) {
 
 // A new state: the step counter, the residual reference and the timeout
 // report start again (a batch's view leaves the batch's report alone).
+// The error a nonzero status word of the step kernels reports.
+lbm_status status_error(lbm_handle* h, int kstatus) {
+    if (kstatus & lbm::kStatusBounds) {
+        set_err(h, "a device bounds check failed in a step kernel (status %d)", kstatus);
+        return LBM_ERR_BOUNDS;
+    }
+    set_err(h, "a step kernel gave up waiting for its staged data (status %d)", kstatus);
+    return LBM_ERR_TIMEOUT;
+}
+
 lbm_status reset_counters(lbm_handle* h) {
     h->steps = 0;
     h->have_prev = 0;
@@ -442,6 +453,8 @@ lbm_status reset_counters(lbm_handle* h) {
 }  // namespace
 
 extern "C" {
+
+int lbm_build_flags(void) { return lbm::kChecked ? LBM_BUILD_CHECKED : 0; }
 
 lbm_status lbm_params_init(lbm_params* p) {
     if (!p) return LBM_ERR_INVALID;
@@ -462,6 +475,7 @@ lbm_status lbm_params_init(lbm_params* p) {
 
 lbm_status lbm_create(const lbm_params* p, const uint8_t* solid_mask, void* cuda_stream,
                       lbm_handle** out) {
+    LBM_RANGE("lbm_create");
     if (!out) {
         set_err(nullptr, "out is NULL");
         return LBM_ERR_INVALID;
@@ -582,6 +596,7 @@ void lbm_destroy(lbm_handle* h) {
 
 lbm_status lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
                            const double* uy, int on_device) {
+    LBM_RANGE("lbm_init_fields");
     if (!h) return LBM_ERR_INVALID;
     const double* in[3] = {rho, ux, uy};
     const double* d[3];
@@ -598,6 +613,7 @@ lbm_status lbm_init_fields(lbm_handle* h, const double* rho, const double* ux,
 }
 
 lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
+    LBM_RANGE("lbm_step");
     if (!h) return LBM_ERR_INVALID;
     if (nsteps < 0) {
         set_err(h, "nsteps must be >= 0");
@@ -658,6 +674,7 @@ lbm_status lbm_debug_fail_alloc(int64_t nth) {
 }
 
 lbm_status lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, int on_device) {
+    LBM_RANGE("lbm_moments");
     if (!h) return LBM_ERR_INVALID;
     const size_t N = (size_t)h->N;
     double* d[3] = {rho, ux, uy};
@@ -685,6 +702,7 @@ lbm_status lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, int o
 
 lbm_status lbm_stress(lbm_handle* h, double* dxux, double* dyuy, double* sxy, double* txx,
                       double* tyy, double* txy, int on_device) {
+    LBM_RANGE("lbm_stress");
     if (!h) return LBM_ERR_INVALID;
     const size_t N = (size_t)h->N;
     double* outs[6] = {dxux, dyuy, sxy, txx, tyy, txy};
@@ -723,6 +741,7 @@ lbm_status lbm_stress(lbm_handle* h, double* dxux, double* dyuy, double* sxy, do
 }
 
 lbm_status lbm_get_f(lbm_handle* h, double* f, int on_device) {
+    LBM_RANGE("lbm_get_f");
     if (!h || !f) return LBM_ERR_INVALID;
     const size_t n = 9 * (size_t)h->N;
     double* d = f;
@@ -745,6 +764,7 @@ lbm_status lbm_get_f(lbm_handle* h, double* f, int on_device) {
 }
 
 lbm_status lbm_set_f(lbm_handle* h, const double* f, int on_device) {
+    LBM_RANGE("lbm_set_f");
     if (!h || !f) return LBM_ERR_INVALID;
     const double* in[1] = {f};
     const double* d[1];
@@ -803,6 +823,7 @@ double fixed_to_double(const long long L[lbm::kMassLimbs]) {
 extern "C" {
 
 lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]) {
+    LBM_RANGE("lbm_diagnostics");
     if (!h || !out) return LBM_ERR_INVALID;
     if (!h->uprev) CK(h, lbm::dev_alloc(&h->uprev, 2 * (size_t)h->N * sizeof(double)), "cudaMalloc(residual)");
     const AuxParams a = aux(h);
@@ -824,10 +845,7 @@ lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]) {
     CK(h, cudaMemcpyAsync(&kstatus, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
        "cudaMemcpyAsync(D2H)");
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    if (kstatus) {
-        set_err(h, "a step kernel gave up waiting for its staged data (status %d)", kstatus);
-        return LBM_ERR_TIMEOUT;
-    }
+    if (kstatus) return status_error(h, kstatus);
     out[0] = fixed_to_double(r.limb) + (double)h->n_fluid * h->p.rho0;
     out[1] = r.mx;
     out[2] = r.my;
@@ -851,6 +869,7 @@ lbm_status lbm_diagnostics(lbm_handle* h, double out[LBM_DIAG_COUNT]) {
 size_t lbm_state_bytes(const lbm_handle* h) { return h ? buf_bytes(h) : 0; }
 
 lbm_status lbm_get_state(lbm_handle* h, void* host, size_t bytes) {
+    LBM_RANGE("lbm_get_state");
     if (!h || !host) return LBM_ERR_INVALID;
     if (bytes != buf_bytes(h)) {
         set_err(h, "state buffer is %zu bytes, expected %zu", bytes, buf_bytes(h));
@@ -863,6 +882,7 @@ lbm_status lbm_get_state(lbm_handle* h, void* host, size_t bytes) {
 }
 
 lbm_status lbm_set_state(lbm_handle* h, const void* host, size_t bytes) {
+    LBM_RANGE("lbm_set_state");
     if (!h || !host) return LBM_ERR_INVALID;
     if (bytes != buf_bytes(h)) {
         set_err(h, "state buffer is %zu bytes, expected %zu", bytes, buf_bytes(h));
@@ -920,6 +940,7 @@ NoAllocDevice g_noalloc[kNoAllocMaxDevices];
 }  // namespace
 
 extern "C" lbm_status lbm_diagnostics_noalloc(lbm_handle* h, double out[LBM_DIAG_COUNT]) {
+    LBM_RANGE("lbm_diagnostics_noalloc");
     if (!h || !out) return LBM_ERR_INVALID;
     if (h->N > kNoAllocMaxCells) {
         set_err(h, "lbm_diagnostics_noalloc: the lattice has %lld cells, its fixed scratch "
@@ -971,8 +992,7 @@ extern "C" lbm_status lbm_diagnostics_noalloc(lbm_handle* h, double out[LBM_DIAG
     CK(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (kstatus) {
         // the state is not valid: no values, and no residual reference taken
-        set_err(h, "a step kernel gave up waiting for its staged data (status %d)", kstatus);
-        return LBM_ERR_TIMEOUT;
+        return status_error(h, kstatus);
     }
     out[0] = fixed_to_double(r.limb) + (double)h->n_fluid * h->p.rho0;
     out[1] = r.mx;
@@ -1233,6 +1253,7 @@ extern "C" {
 lbm_status lbm_batch_create(const lbm_params* params, int count,
                             const uint8_t* const* solid_masks, void* cuda_stream,
                             lbm_batch** out) {
+    LBM_RANGE("lbm_batch_create");
     if (!out) {
         set_err(nullptr, "out is NULL");
         return LBM_ERR_INVALID;
@@ -1395,6 +1416,7 @@ int lbm_batch_count(const lbm_batch* b) { return b ? b->count : -1; }
 
 lbm_status lbm_batch_init_fields(lbm_batch* b, int k, const double* rho, const double* ux,
                                  const double* uy, int on_device) {
+    LBM_RANGE("lbm_batch_init_fields");
     if (bad_index(b, k)) return LBM_ERR_INVALID;
     lbm_handle h;
     make_view(b, k, h);
@@ -1501,6 +1523,7 @@ lbm_status advance(lbm_batch* b, int64_t nsteps, bool graphs) {
 extern "C" {
 
 lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+    LBM_RANGE("lbm_batch_step");
     if (!b) return LBM_ERR_INVALID;
     if (nsteps < 0) {
         bset_err(b, "nsteps must be >= 0");
@@ -1510,6 +1533,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
 }
 
 lbm_status lbm_batch_residuals(lbm_batch* b, double* res) {
+    LBM_RANGE("lbm_batch_residuals");
     if (!b) return LBM_ERR_INVALID;
     if (lbm_status s = upload_list(b); s != LBM_OK) return s;
     const int C = b->count;
@@ -1538,6 +1562,11 @@ lbm_status lbm_batch_residuals(lbm_batch* b, double* res) {
         // active in the steps since the last check hold invalid states
         BCK(b, cudaMemsetAsync(b->status, 0, sizeof(int), b->stream), "cudaMemsetAsync(status)");
         BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+        if (kstatus & lbm::kStatusBounds) {
+            bset_err(b, "a device bounds check failed in a batch step kernel (status %d)",
+                     kstatus);
+            return LBM_ERR_BOUNDS;
+        }
         bset_err(b, "a batch step kernel gave up waiting for its staged data (status %d)", kstatus);
         return LBM_ERR_TIMEOUT;
     }
@@ -1569,6 +1598,7 @@ lbm_status lbm_batch_residuals(lbm_batch* b, double* res) {
 
 lbm_status lbm_batch_run(lbm_batch* b, double tol, int64_t check_every, int64_t max_steps,
                          double* res) {
+    LBM_RANGE("lbm_batch_run");
     if (!b) return LBM_ERR_INVALID;
     if (!(tol >= 0.0) || check_every < 1 || max_steps < 0) {
         bset_err(b, "need tol >= 0, check_every >= 1 and max_steps >= 0");
@@ -1610,6 +1640,7 @@ lbm_status lbm_batch_run(lbm_batch* b, double tol, int64_t check_every, int64_t 
 }
 
 lbm_status lbm_batch_tune(lbm_batch* b, int trial_steps, int* block_x, int* rows_per_band) {
+    LBM_RANGE("lbm_batch_tune");
     if (!b) return LBM_ERR_INVALID;
     if (trial_steps < 1) {
         bset_err(b, "trial_steps must be >= 1");
@@ -1660,6 +1691,7 @@ lbm_status lbm_batch_tune(lbm_batch* b, int trial_steps, int* block_x, int* rows
 
 lbm_status lbm_batch_moments(lbm_batch* b, int k, double* rho, double* ux, double* uy,
                              int on_device) {
+    LBM_RANGE("lbm_batch_moments");
     if (bad_index(b, k)) return LBM_ERR_INVALID;
     lbm_handle h;
     make_view(b, k, h);
@@ -1667,6 +1699,7 @@ lbm_status lbm_batch_moments(lbm_batch* b, int k, double* rho, double* ux, doubl
 }
 
 lbm_status lbm_batch_get_f(lbm_batch* b, int k, double* f, int on_device) {
+    LBM_RANGE("lbm_batch_get_f");
     if (bad_index(b, k)) return LBM_ERR_INVALID;
     lbm_handle h;
     make_view(b, k, h);
@@ -1674,6 +1707,7 @@ lbm_status lbm_batch_get_f(lbm_batch* b, int k, double* f, int on_device) {
 }
 
 lbm_status lbm_batch_diagnostics(lbm_batch* b, int k, double out[LBM_DIAG_COUNT]) {
+    LBM_RANGE("lbm_batch_diagnostics");
     if (bad_index(b, k) || !out) return LBM_ERR_INVALID;
     lbm_handle h;
     make_view(b, k, h);

@@ -83,6 +83,48 @@ struct AuxParams {
     const uint8_t* __restrict__ lmask;
 };
 
+// Device bounds checks of the checked build (compiled with LBM_CHECKED):
+// every computed population index is tested against the buffer's 9 * plane
+// elements, every link-mask index against pitch * ny, every shared-memory
+// index against its array.  A failed test sets the caller's `bad` flag and
+// skips the access (a load gives 0); the kernel then records bit 1 of its
+// status word and its block stops at the next point where it can, without
+// a trap.  In the normal build the tests compile away.
+#ifdef LBM_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+constexpr int kStatusTimeout = 1;  // status bit: a bounded wait ran out
+constexpr int kStatusBounds = 2;   // status bit: a bounds check failed (checked build)
+
+template <typename I>
+__device__ __forceinline__ bool idx_ok(I i, long long n, int width = 1) {
+    return (long long)i >= 0 && (long long)i + width <= n;
+}
+// Global read-only load of p[i], checked against n elements.
+template <typename S, typename I>
+__device__ __forceinline__ S ldg_chk(const S* __restrict__ p, I i, long long n, bool& bad) {
+    if constexpr (kChecked) {
+        if (!idx_ok(i, n)) {
+            bad = true;
+            return S(0);
+        }
+    }
+    return __ldg(p + i);
+}
+// Link-mask byte of cell (x, y), checked.
+template <typename P>
+__device__ __forceinline__ unsigned mask_at(const P& p, long long i, bool& bad) {
+    if constexpr (kChecked) {
+        if (!idx_ok(i, (long long)p.pitch * p.ny)) {
+            bad = true;
+            return 0xFFu;
+        }
+    }
+    return p.lmask[i];
+}
+
 // Bit i-1 (i = 1..8) is set when the source node x - e_i of direction i is a
 // wall or solid node.  With a mask the bits are precomputed per cell (0xFF
 // marks a solid cell); without one the walls are the non-periodic domain
@@ -119,6 +161,41 @@ __device__ __forceinline__ void pull(const S* __restrict__ fin, const P& p, int 
     f[6] = __ldg(fin + ((sb & 32u) ? 8 * pl + c : 6 * pl + rm + xp));
     f[7] = __ldg(fin + ((sb & 64u) ? 5 * pl + c : 7 * pl + rp + xp));
     f[8] = __ldg(fin + ((sb & 128u) ? 6 * pl + c : 8 * pl + rp + xm));
+}
+
+// pull() with its nine indices checked in the checked build.
+template <typename S, typename P>
+__device__ __forceinline__ void pull(const S* __restrict__ fin, const P& p, int x, int y,
+                                     unsigned sb, S f[9], bool& bad) {
+    if constexpr (kChecked) {
+        const int xm = x == 0 ? p.nx - 1 : x - 1;
+        const int xp = x == p.nx - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? p.ny - 1 : y - 1;
+        const int yp = y == p.ny - 1 ? 0 : y + 1;
+        const long long pl = p.plane, n = 9 * pl;
+        const long long rc = (long long)y * p.rstride, rm = (long long)ym * p.rstride,
+                        rp = (long long)yp * p.rstride;
+        const long long c = rc + x;
+        bool ok = x >= 0 && x < p.nx && y >= 0 && y < p.ny;
+        const long long idx[9] = {c,
+                                  (sb & 1u) ? 3 * pl + c : 1 * pl + rc + xm,
+                                  (sb & 2u) ? 4 * pl + c : 2 * pl + rm + x,
+                                  (sb & 4u) ? 1 * pl + c : 3 * pl + rc + xp,
+                                  (sb & 8u) ? 2 * pl + c : 4 * pl + rp + x,
+                                  (sb & 16u) ? 7 * pl + c : 5 * pl + rm + xm,
+                                  (sb & 32u) ? 8 * pl + c : 6 * pl + rm + xp,
+                                  (sb & 64u) ? 5 * pl + c : 7 * pl + rp + xp,
+                                  (sb & 128u) ? 6 * pl + c : 8 * pl + rp + xm};
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ok = ok && idx_ok(idx[i], n);
+        if (!ok) {
+            bad = true;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = S(0);
+            return;
+        }
+    }
+    pull(fin, p, x, y, sb, f);
 }
 
 // 1-D three-velocity Maxwell-matched factors of the equilibrium

@@ -32,6 +32,7 @@
 
 #include "lbm_nn.h"
 #include "dev_alloc.h"
+#include "nvtx_range.h"
 
 namespace {
 
@@ -1137,6 +1138,7 @@ extern "C" {
 
 lbm_status lbm_nn_create(int levels, const int* channels, int max_batch, int height, int width,
                          uint64_t seed, void* cuda_stream, lbm_nn** out) {
+    LBM_RANGE("lbm_nn_create");
     if (!out) {
         nn_err(nullptr, "out is NULL");
         return LBM_ERR_INVALID;
@@ -1356,6 +1358,7 @@ lbm_status lbm_nn_set_params(lbm_nn* nn, const float* params) {
 }
 
 lbm_status lbm_nn_forward(lbm_nn* nn, const float* x, int n, float* y) {
+    LBM_RANGE("lbm_nn_forward");
     if (!nn || !x || !y) return LBM_ERR_INVALID;
     if (bad_batch(nn, n)) return LBM_ERR_INVALID;
     lbm_status s = upload_inputs(nn, x, nullptr, nullptr, n);
@@ -1371,6 +1374,7 @@ lbm_status lbm_nn_forward(lbm_nn* nn, const float* x, int n, float* y) {
 
 lbm_status lbm_nn_gradients(lbm_nn* nn, const float* x, const float* target,
                             const uint8_t* fluid, int n, float* loss, float* grads) {
+    LBM_RANGE("lbm_nn_gradients");
     if (!nn || !x || !target || !fluid) return LBM_ERR_INVALID;
     if (bad_batch(nn, n)) return LBM_ERR_INVALID;
     lbm_status s = upload_inputs(nn, x, target, fluid, n);
@@ -1383,6 +1387,7 @@ lbm_status lbm_nn_gradients(lbm_nn* nn, const float* x, const float* target,
 
 lbm_status lbm_nn_train_step(lbm_nn* nn, const float* x, const float* target,
                              const uint8_t* fluid, int n, float lr, float* loss) {
+    LBM_RANGE("lbm_nn_train_step");
     if (!nn || !x || !target || !fluid) return LBM_ERR_INVALID;
     if (bad_batch(nn, n)) return LBM_ERR_INVALID;
     if (!(lr > 0.0f) || !std::isfinite(lr)) {

@@ -13,7 +13,9 @@
 //      (central differences; a wall or solid neighbour mirrors the cell's
 //      own density), collides, adds the moving-wall term and stores;
 //   4. cluster barrier; the buffers swap.
-// Every CTA runs the same number of steps and barriers, with no early exit.
+// Every CTA runs the same number of steps and barriers, with no early exit
+// (a checked build skips an access that fails its bounds test and records
+// bit 1 of the status word at the end).
 // The arithmetic is that of step_block in the same order (the FP32 collision
 // on a float2 lane pair whose lanes are independent), so a lattice goes
 // through the same states bit for bit on either path.
@@ -34,7 +36,7 @@ constexpr int kSmallThreads = 256;  // per CTA; a CTA loops over its band's cell
 // the cluster within the launch)
 template <typename S, typename P>
 __device__ __forceinline__ void pull_l2(const S* fin, const P& p, int x, int y, unsigned sb,
-                                        S f[9]) {
+                                        S f[9], bool& bad) {
     const int xm = x == 0 ? p.nx - 1 : x - 1;
     const int xp = x == p.nx - 1 ? 0 : x + 1;
     const int ym = y == 0 ? p.ny - 1 : y - 1;
@@ -43,6 +45,27 @@ __device__ __forceinline__ void pull_l2(const S* fin, const P& p, int x, int y, 
     const long long rc = (long long)y * p.rstride, rm = (long long)ym * p.rstride,
                     rp = (long long)yp * p.rstride;
     const long long c = rc + x;
+    if constexpr (kChecked) {
+        const long long n = 9 * pl;
+        const long long idx[9] = {c,
+                                  (sb & 1u) ? 3 * pl + c : 1 * pl + rc + xm,
+                                  (sb & 2u) ? 4 * pl + c : 2 * pl + rm + x,
+                                  (sb & 4u) ? 1 * pl + c : 3 * pl + rc + xp,
+                                  (sb & 8u) ? 2 * pl + c : 4 * pl + rp + x,
+                                  (sb & 16u) ? 7 * pl + c : 5 * pl + rm + xm,
+                                  (sb & 32u) ? 8 * pl + c : 6 * pl + rm + xp,
+                                  (sb & 64u) ? 5 * pl + c : 7 * pl + rp + xp,
+                                  (sb & 128u) ? 6 * pl + c : 8 * pl + rp + xm};
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ok = ok && idx_ok(idx[i], n);
+        if (!ok) {
+            bad = true;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = S(0);
+            return;
+        }
+    }
     f[0] = __ldcg(fin + c);
     f[1] = __ldcg(fin + ((sb & 1u) ? 3 * pl + c : 1 * pl + rc + xm));
     f[2] = __ldcg(fin + ((sb & 2u) ? 4 * pl + c : 2 * pl + rm + x));
@@ -69,41 +92,62 @@ __global__ void __launch_bounds__(kSmallThreads) small_run_kernel(T* f0, T* f1, 
     const int b = (int)blockIdx.x;
     const int y0 = (int)((long long)b * p.ny / C), y1 = (int)((long long)(b + 1) * p.ny / C);
     const int ncell = (y1 - y0) * p.nx;
+    const long long ncells = (long long)p.nx * p.ny;  // elements of the density field
+    bool bad = false;  // checked build: a failed bounds check (the access is skipped)
+    auto bits = [&](int x, int y) -> unsigned {
+        if constexpr (MASK) return mask_at(p, (long long)y * p.pitch + x, bad);
+        return link_bits<false>(p, x, y);
+    };
+    auto dload = [&](long long i) -> T {
+        if (kChecked && !idx_ok(i, ncells)) {
+            bad = true;
+            return T(0);
+        }
+        return __ldcg(dfield + i);
+    };
     for (int s = 0; s < nsteps; ++s) {
         const T* fin = ((from + s) & 1) ? f1 : f0;
         T* fout = ((from + s) & 1) ? f0 : f1;
         // 1. densities
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
             const int y = y0 + c / p.nx, x = c % p.nx;
-            const unsigned sb = link_bits<MASK>(p, x, y);
+            const unsigned sb = bits(x, y);
             T d = T(0);
             if (sb != 0xFFu) {
                 T g[9];
-                pull_l2(fin, p, x, y, sb, g);
+                pull_l2(fin, p, x, y, sb, g, bad);
                 d = dens(g);
             }
-            dfield[(long long)y * p.nx + x] = d;
+            const long long di = (long long)y * p.nx + x;
+            if (kChecked && !idx_ok(di, ncells))
+                bad = true;
+            else
+                dfield[di] = d;
         }
         cluster.sync();
         // 3. collide and store
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
             const int y = y0 + c / p.nx, x = c % p.nx;
-            const unsigned sb = link_bits<MASK>(p, x, y);
+            const unsigned sb = bits(x, y);
             const long long o = (long long)y * p.rstride + x;
+            if (kChecked && !(y >= 0 && y < p.ny && x >= 0 && x < p.rstride)) {
+                bad = true;
+                continue;
+            }
             T g[9];
             if (sb == 0xFFu) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) fout[i * p.plane + o] = T(0);
                 continue;
             }
-            pull_l2(fin, p, x, y, sb, g);
+            pull_l2(fin, p, x, y, sb, g, bad);
             const T d = dens(g);
             const int xw = x == 0 ? p.nx - 1 : x - 1, xe = x == p.nx - 1 ? 0 : x + 1;
             const int ys = y == 0 ? p.ny - 1 : y - 1, yn = y == p.ny - 1 ? 0 : y + 1;
-            const T dW = (sb & 1u) ? d : __ldcg(dfield + (long long)y * p.nx + xw);
-            const T dS = (sb & 2u) ? d : __ldcg(dfield + (long long)ys * p.nx + x);
-            const T dE = (sb & 4u) ? d : __ldcg(dfield + (long long)y * p.nx + xe);
-            const T dN = (sb & 8u) ? d : __ldcg(dfield + (long long)yn * p.nx + x);
+            const T dW = (sb & 1u) ? d : dload((long long)y * p.nx + xw);
+            const T dS = (sb & 2u) ? d : dload((long long)ys * p.nx + x);
+            const T dE = (sb & 4u) ? d : dload((long long)y * p.nx + xe);
+            const T dN = (sb & 8u) ? d : dload((long long)yn * p.nx + x);
             const T dxr = T(0.5) * (dE - dW);
             const T dyr = p.iah * (dN - dS);
             T rho = p.rho0 + d;
@@ -133,6 +177,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_run_kernel(T* f0, T* f1, 
         }
         cluster.sync();
     }
+    if (kChecked && bad) atomicOr(p.status, kStatusBounds);
 }
 
 template <typename T, bool MASK>

@@ -45,7 +45,9 @@
 //
 // Every mbarrier wait is bounded.  A wait that runs out sets bit 0 of
 // *p.status, waits (bounded again) for the block's copies still in flight,
-// and the whole block returns.
+// and the whole block returns.  A checked build (LBM_CHECKED) also tests
+// every computed global, mask and shared-memory index; a failed test skips
+// the access, sets bit 1 and stops the block the same way.
 #pragma once
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
@@ -171,6 +173,10 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     T* stage = reinterpret_cast<T*>(smem + 128);        // [kStages][9][SW]
     T* ring = stage + kStages * 9 * SW;                 // [4][RW], column c at c - x0 + 4
     const uint8_t* smask = reinterpret_cast<const uint8_t*>(ring + 4 * RW);  // [kStages][W]
+    // checked build: a failed bounds check (the access is skipped; the block
+    // stops at its next vote)
+    bool bad = false;
+    const long long nbuf = 9 * (long long)p.plane;  // elements of a population buffer
 
     const int tx = threadIdx.x;
     const int lane = tx & 31;
@@ -226,7 +232,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     auto row_valid = [&](int r) { return (r >= 0 && r < p.ny) || p.py; };
     auto wrap_row = [&](int r) { return r < 0 ? r + p.ny : (r >= p.ny ? r - p.ny : r); };
     auto bits_at = [&](int cx, int rr) -> unsigned {
-        if (MASK) return p.lmask[(I)rr * pitch + cx];
+        if (MASK) return mask_at(p, (long long)rr * pitch + cx, bad);
         const unsigned Wb = (cx == 0) & !p.px, Eb = (cx == p.nx - 1) & !p.px;
         const unsigned S = (rr == 0) & !p.py, N = (rr == p.ny - 1) & !p.py;
         return Wb | (S << 1) | (Eb << 2) | (N << 3) | ((Wb | S) << 4) | ((Eb | S) << 5) |
@@ -248,6 +254,14 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         unsigned any = 0;
         if (MASK) {
             const uint8_t* m = smask + s * W + c0;
+            if constexpr (kChecked) {
+                if (!idx_ok(s * W + c0, kStages * W, VC)) {
+                    bad = true;
+#pragma unroll
+                    for (int j = 0; j < VC; ++j) sb[j] = 0xFFu;
+                    return 0xFFu;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < VC; ++j) {
                 sb[j] = (c0 + j < nseg) ? (unsigned)m[j] : 0xFFu;
@@ -291,13 +305,31 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
             }
             srow[e] = sr;
         }
+        if constexpr (kChecked) {
+            // a copy stays inside its source row and its stage row
+            const bool cols_ok = wstart >= 0 && wend <= (int)rs && wstart < wend &&
+                                 dshift >= 0 && dshift + (wend - wstart) <= SW;
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                if (srow[e] >= p.ny || (srow[e] >= 0 && !cols_ok)) {
+                    bad = true;
+                    srow[e] = -1;
+                }
+        }
+        bool mcopy = MASK && ok;
+        if constexpr (kChecked) {
+            if (mcopy && !idx_ok((long long)rr * pitch + x0, (long long)pitch * p.ny, (int)mbytes)) {
+                bad = true;
+                mcopy = false;
+            }
+        }
         unsigned bytes = 0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int sr = srow[ey(i) == 0 ? 0 : (ey(i) > 0 ? 1 : 2)];
             if (sr >= 0) bytes += cbytes;
         }
-        if (MASK && ok) bytes += mbytes;
+        if (mcopy) bytes += mbytes;
         mbar_expect_tx(bar, bytes);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -306,7 +338,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                 bulk_g2s(st0 + (unsigned)(((s * 9 + i) * SW + dshift) * sizeof(T)),
                          fin + (i * pl + (I)sr * rs + wstart), cbytes, bar);
         }
-        if (MASK && ok)
+        if (mcopy)
             bulk_g2s(sm0 + (unsigned)(s * W), p.lmask + ((I)rr * pitch + x0), mbytes, bar);
     };
     // (spreading the ten copies over warps 1-3 measured 5 % slower than one
@@ -322,6 +354,19 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     // a periodic x axis; zeros for a solid or inactive cell.
     auto load = [&](int s, int rr, const unsigned* sb, bool fast, T (*g)[VC]) {
         const T* b = stage + s * 9 * SW + (c0 + kHalo);
+        if constexpr (kChecked) {
+            // every stage read below lies in columns c0 + kHalo - 1 .. c0 +
+            // kHalo + VC of the nine rows of stage s
+            if (!(idx_ok(s * 9 * SW + c0 + kHalo - 1, kStages * 9 * SW) &&
+                  idx_ok((s * 9 + 8) * SW + c0 + kHalo + VC, kStages * 9 * SW))) {
+                bad = true;
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+#pragma unroll
+                    for (int j = 0; j < VC; ++j) g[i][j] = T(0);
+                return;
+            }
+        }
         if (fast) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -365,13 +410,13 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                             if (ey(i) == 0)
                                 f[i] = b[opp(i) * SW + j];
                             else
-                                f[i] = __ldg(fin + (opp(i) * pl + (I)rr * rs + cx));
+                                f[i] = ldg_chk(fin, opp(i) * pl + (I)rr * rs + cx, nbuf, bad);
                         } else {
                             f[i] = b[i * SW + j - ex(i)];
                         }
                     }
                 } else {
-                    pull(fin, p, cx, rr, sb[j], f);
+                    pull(fin, p, cx, rr, sb[j], f, bad);
                 }
 #pragma unroll
                 for (int i = 0; i < 9; ++i) g[i][j] = f[i];
@@ -441,7 +486,12 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
             }
             colc = true;
         }
-        if (all_active) {
+        if constexpr (kChecked) {
+            if (!idx_ok(slot * RW + c0 + 4, 4 * RW, VC)) bad = true;
+        }
+        if (kChecked && bad) {
+            // a checked build skips the ring row after a failed check
+        } else if (all_active) {
             stv<T, VC>(ring + slot * RW + c0 + 4, dc);
         } else {  // a partial last group must not touch the right halo's slot
 #pragma unroll
@@ -455,14 +505,18 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                 if (hb != 0xFFu) {
                     const int i = hi;
                     if (hb == 0u && !hwrap) {
-                        h = stage[(s * 9 + i) * SW + (hx - x0 + kHalo - ex(i))];
+                        const int si = (s * 9 + i) * SW + (hx - x0 + kHalo - ex(i));
+                        if (kChecked && !idx_ok(si, kStages * 9 * SW))
+                            bad = true;
+                        else
+                            h = stage[si];
                     } else if (i > 0 && ((hb >> (i - 1)) & 1u)) {
-                        h = __ldg(fin + (opp(i) * pl + (I)rr * rs + hx));
+                        h = ldg_chk(fin, opp(i) * pl + (I)rr * rs + hx, nbuf, bad);
                     } else {
                         int sx = hx - ex(i), sy = rr - ey(i);
                         sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
                         sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
-                        h = __ldg(fin + (i * pl + (I)sy * rs + sx));
+                        h = ldg_chk(fin, i * pl + (I)sy * rs + sx, nbuf, bad);
                     }
                 }
             }
@@ -471,13 +525,21 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
             // block computes it
 #pragma unroll
             for (int off = 1; off < 16; off <<= 1) h += __shfl_xor_sync(0xffffffffu, h, off);
-            if (hi == 0 && hok) ring[slot * RW + (hside == 0 ? 3 : nseg + 4)] = h;
+            if (hi == 0 && hok) {
+                const int ri = slot * RW + (hside == 0 ? 3 : nseg + 4);
+                if (kChecked && !idx_ok(ri, 4 * RW))
+                    bad = true;
+                else
+                    ring[ri] = h;
+            }
         }
 
-        // 2. barrier, with a vote on a timed-out wait
-        if (__syncthreads_or(to)) {
+        // 2. barrier, with a vote on a timed-out wait (and, in a checked
+        // build, on a failed bounds check)
+        if (__syncthreads_or(to || (kChecked && bad))) {
+            if (to) atomicOr(p.status, kStatusTimeout);
+            if (kChecked && bad) atomicOr(p.status, kStatusBounds);
             if (tx == 0) {
-                atomicOr(p.status, 1);
                 // copies issued for iterations k .. k+kStages-1 may be in flight
                 for (int j = k; j < k + kStages && j < nit; ++j)
                     mbar_wait(bar0 + 8u * (j % kStages), (unsigned)((j / kStages) & 1));
@@ -499,6 +561,12 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
             const int sN = dir > 0 ? (k & 3) : ((k - 2) & 3);
             const int sS = dir > 0 ? ((k - 2) & 3) : (k & 3);
             T dCv[VC + 2], dNv[VC], dSv[VC];
+            if constexpr (kChecked) {
+                // ring reads: columns c0 + 3 .. c0 + 4 + VC of rows sC, sN, sS
+                if (!(idx_ok(sC * RW + c0 + 3, 4 * RW, VC + 2) &&
+                      idx_ok(sN * RW + c0 + 4, 4 * RW, VC) && idx_ok(sS * RW + c0 + 4, 4 * RW, VC)))
+                    bad = true;
+            }
             ldv<T, VC>(ring + sC * RW + c0 + 4, dCv + 1);
             dCv[0] = ring[sC * RW + c0 + 3];
             dCv[VC + 1] = ring[sC * RW + c0 + 4 + VC];
@@ -576,8 +644,13 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                 }
             }
             const I o = (I)rc * rs + xa;
+            if constexpr (kChecked) {
+                if (!(rc >= 0 && rc < p.ny && xa >= 0 && xa + VC <= (int)rs)) bad = true;
+            }
+            if (!(kChecked && bad)) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) stv<T, VC>(fout + (i * pl + o), gcol[i]);
+                for (int i = 0; i < 9; ++i) stv<T, VC>(fout + (i * pl + o), gcol[i]);
+            }
         }
 #pragma unroll
         for (int j = 0; j < VC; ++j) { sbp[j] = sbc[j]; dp[j] = dc[j]; }
@@ -594,6 +667,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
     __syncthreads();
     if (tx == 0)
         for (int s = 0; s < kStages; ++s) mbar_inval(bar0 + 8u * s);
+    if (kChecked && bad) atomicOr(p.status, kStatusBounds);  // after the last vote
     __syncthreads();
     return true;
 }

@@ -17,7 +17,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
+# LBM_CHECKED=1 in the environment loads the checked build (device bounds
+# checks in the step kernels; ``build(checked=True)``) instead.
+CHECKED = os.environ.get("LBM_CHECKED", "") == "1"
+LIB_PATH = os.path.join(_HERE, "liblbm_gb300_checked.so" if CHECKED else "liblbm_gb300.so")
 
 LBM_OK = 0
 LBM_ERR_INVALID = -1
@@ -26,11 +29,14 @@ LBM_ERR_CUDA = -3
 LBM_ERR_UNSTABLE = -4
 LBM_ERR_TIMEOUT = -5
 LBM_ERR_STATE = -6
+LBM_ERR_BOUNDS = -7
+LBM_BUILD_CHECKED = 1
 LBM_DIAG_COUNT = 8
 DIAG_NAMES = ("mass", "mom_x", "mom_y", "energy", "residual", "nonfinite", "step",
               "step_change")
 _STATUS = {0: "LBM_OK", -1: "LBM_ERR_INVALID", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA",
-           -4: "LBM_ERR_UNSTABLE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE"}
+           -4: "LBM_ERR_UNSTABLE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE",
+           -7: "LBM_ERR_BOUNDS"}
 
 
 class LbmError(RuntimeError):
@@ -65,8 +71,10 @@ def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
             f"{LIB_PATH} is not built; build it with __graft_entry__.build() "
-            "(nvcc, sm_103a).  There is no CPU fallback.")
+            "(nvcc, sm_103a; the checked build with build(checked=True)).  "
+            "There is no CPU fallback.")
     L = ctypes.CDLL(LIB_PATH)
+    L.lbm_build_flags.argtypes = []
     L.lbm_params_init.argtypes = [ctypes.POINTER(lbm_params)]
     L.lbm_create.argtypes = [ctypes.POINTER(lbm_params), ctypes.POINTER(ctypes.c_uint8), _P,
                              ctypes.POINTER(_P)]
