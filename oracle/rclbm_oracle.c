@@ -143,7 +143,7 @@ static void build_F(double a, double ux, double uy, const double* Ti,
 int orc_matrices(double a, double ux, double uy, double T[81], double Ti[81],
                  double F[81], double Fi[81])
 {
-    if (!(a > 0.0)) return -1;
+    if (!(a > 0.0) || !T || !Ti || !F || !Fi) return -1;
     build_T(a, T);
     if (invert9(T, Ti)) return -1;
     build_F(a, ux, uy, Ti, F);
@@ -154,6 +154,7 @@ int orc_matrices(double a, double ux, double uy, double T[81], double Ti[81],
 int orc_central_moments(double a, const double f[9], double ux, double uy,
                         double kc[9])
 {
+    if (!f || !kc) return -1;
     /* Eq. 43 summed directly. */
     for (int k = 0; k < 9; ++k) {
         double s = 0.0;
@@ -183,7 +184,7 @@ int orc_feq(double a, double cs2, double rho, double ux, double uy,
             double feq[9])
 {
     double T[81], Ti[81];
-    if (!(a > 0.0)) return -1;
+    if (!(a > 0.0) || !feq) return -1;
     build_T(a, T);
     if (invert9(T, Ti)) return -1;
     feq_with(Ti, a, cs2, rho, ux, uy, feq);
@@ -333,7 +334,7 @@ int orc_collide_cell(const orc_params* p, const double f[9], double dxrho,
                      double dyrho, double ft[9], double strain[2])
 {
     double T[81], Ti[81];
-    if (!p || !(p->a > 0.0) || !(p->omega[3] > 0.0) || !(p->omega[4] > 0.0))
+    if (!p || !f || !ft || !(p->a > 0.0) || !(p->omega[3] > 0.0) || !(p->omega[4] > 0.0))
         return -1;
     build_T(p->a, T);
     if (invert9(T, Ti)) return -1;
