@@ -68,14 +68,14 @@ def parse():
     ap.add_argument("--ttr-max-steps", type=int, default=60000)
     ap.add_argument("--no-warm", action="store_true",
                     help="skip the learned warm-start measurement")
-    ap.add_argument("--warm-train", type=int, default=1024)
-    ap.add_argument("--warm-n", type=int, default=32,
+    ap.add_argument("--warm-train", type=int, default=2000)
+    ap.add_argument("--warm-n", type=int, default=64,
                     help="cavity size n x n of the warm-start instances")
-    ap.add_argument("--warm-test", type=int, default=32,
+    ap.add_argument("--warm-test", type=int, default=1000,
                     help="held-out warm-start instances")
     ap.add_argument("--warm-only", action="store_true",
                     help="print only the warm-start measurement")
-    ap.add_argument("--warm-epochs", type=int, default=60)
+    ap.add_argument("--warm-epochs", type=int, default=40)
     ap.add_argument("--nn-only", action="store_true",
                     help="only the surrogate's forward and training-step times")
     ap.add_argument("--nn-prof", action="store_true",

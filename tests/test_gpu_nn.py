@@ -153,8 +153,9 @@ def test_warm_start_against_rest_start(orc):
     different paths adds ~1e-6 U; measured 1e-6 to 7e-6 U).  Without the
     network's output stage, which gives the prediction no staggered momentum
     (an exact invariant of the scheme, lbm.h), the two differ by up to 12 %.
-    The warm-started state of two instances is then taken, from the same
-    start, to the same residual by the FP64 oracle.  The steps either way are
+    Every instance is then taken from the same predicted start to the same
+    residual by the FP64 oracle, whose final velocities the GPU's match
+    within the same 1e-4 of the lid speed.  The steps either way are
     printed; the gain is measured by bench.py, not asserted here."""
     from paper_2103_02119_gb300 import warmstart as WS
     n = 32
@@ -180,7 +181,7 @@ def test_warm_start_against_rest_start(orc):
         print("instance", k, "max |du| / U rest vs warm", d)
         assert d <= 1e-4, (k, d)
     # the FP64 oracle from the same warm start to the same residual
-    for k in (0, 1):
+    for k in range(len(test)):
         w = test[k]
         p = orc.OracleParams.make(w.nx, w.ny, w.a, w.cs2, w.omega, periodic_x=0, periodic_y=0,
                                   wall_u=w.wall_u)

@@ -110,6 +110,27 @@ def test_tilings_are_bit_identical(precision, block_x, bands):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("periodic", [0, 1])
+def test_narrow_tiles_with_walls(orc, precision, periodic):
+    """Narrow tiles on a lattice with walls, a moving lid and a ragged last
+    segment: with 64-column segments and 7-row bands most blocks see no edge
+    of the lattice, the others see one or two.  The result equals the oracle
+    and, bit for bit, the one-block-wide tiling (one 512-column segment,
+    bands of the whole height)."""
+    wl = _fields(W.cavity(300, 70, 0.5, 0.075, 0.04, 150.0), 13)
+    if periodic:
+        wl = wl.with_(periodic_x=1, periodic_y=1, wall_u=((0.0, 0.0),) * 4)
+    o, g = pair(orc, wl, precision, noise_seed=14, noise_amp=5e-4, block_x=32, bands=10)
+    ref = gpu_of(wl, precision, block_x=256, bands=1)
+    ref.set_f(g.get_f())
+    o.step(9)
+    g.step(9)
+    ref.step(9)
+    compare(o, g, precision)
+    assert ref.get_state() == g.get_state()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
 def test_config1_poiseuille(orc, precision):
     """32 x 32 channel, a = 0.5, nu = 0.1, u_max = 0.01, 5000 steps from rest:
     against the oracle and against the parabola of Sec. 5.1."""
