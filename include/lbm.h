@@ -298,10 +298,19 @@ const char* lbm_last_error(const lbm_handle* h);
  * steady-state residual loop and the autotuner are library plumbing with no
  * counterpart there.
  *
- * Every step of a batch is one launch of a persistent kernel that walks a
- * device work list of (lattice, column segment, band of rows) items of the
- * active lattices (two launches when the batch mixes the RC-LBM and RNR-LBM
- * schemes, one per scheme); runs of 50 steps replay a captured CUDA graph.  Lattices
+ * Every step of a batch is one launch of a persistent kernel per group of
+ * lattices, each walking a list of (lattice, column segment, band of rows)
+ * work items of its group's active lattices.  When they fit, the active
+ * lattices form up to 4 groups of one scheme and at most ~170 lattices
+ * each, whose parameter tables sit in constant memory (one table per group,
+ * shared by every batch of the device: a batch whose tables another batch
+ * has replaced re-uploads them after a device synchronisation; batches
+ * stepped at the same time from several host threads must not use this
+ * path); the groups' kernels run one after another on the batch's stream.
+ * Otherwise one kernel per
+ * scheme reads the parameters from a table in global memory (slower: they
+ * then take vector registers).  Runs of 50 steps replay a captured CUDA
+ * graph.  Lattices
  * can be retired (made inactive) and brought back; an inactive lattice keeps
  * its state and is not stepped.  Conventions as for lbm_handle; work is
  * issued on the stream given to lbm_batch_create.
@@ -371,6 +380,17 @@ int lbm_batch_is_active(const lbm_batch* b, int k);
  * changes the schedule only, never the results.  Default 32, 16. */
 lbm_status lbm_batch_set_shape(lbm_batch* b, int block_x, int rows_per_band);
 lbm_status lbm_batch_get_shape(const lbm_batch* b, int* block_x, int* rows_per_band);
+
+/* Whether the active lattices step from the constant-memory tables when they
+ * fit (enable = 1, the default) or always from the global table (0).  The
+ * choice changes the schedule only, never the results.  Errors:
+ * LBM_ERR_INVALID. */
+lbm_status lbm_batch_set_table_path(lbm_batch* b, int enable);
+
+/* The number of constant-memory table groups the active lattices step in
+ * (0: the global-table kernel), or -1 for a NULL batch or a failed upload of
+ * the work lists. */
+int lbm_batch_table_groups(lbm_batch* b);
 
 /* lbm_set_wait_limit for every lattice of the batch (a test hook): from the
  * next step the batch kernel's row waits give up after `polls` polls; a

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <new>
@@ -1073,6 +1074,17 @@ struct lbm_batch {
     size_t stage_elems = 0;
     int parity = 0;
     int bx = 32, rows = 16, grid = 0;
+    // Constant-memory lattice tables (batch_table.cuh): when the active
+    // lattices fit, they step in up to kBatchTables groups of one scheme
+    // each, group g from table g, one group after another.
+    bool table_path = true;          // use the tables when the lattices fit
+    int ngroups = 0;                 // groups in use; 0: the shared-memory kernel
+    int graw[lbm::kBatchTables] = {};
+    int ggrid[lbm::kBatchTables] = {};
+    std::vector<lbm::BatchTableLattice> gtab[lbm::kBatchTables];
+    int gtotal[lbm::kBatchTables] = {};
+    unsigned long long serial = 0;   // which batch the device's tables hold
+    int device = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t launches = 0;
     char err[512] = {0};
@@ -1136,7 +1148,10 @@ lbm_status set_shape(lbm_batch* b, int bx, int rows) {
 // in d_list / h_list.
 size_t list_at(const lbm_batch* b, int w) { return (size_t)w * (2 * (size_t)b->count + 2); }
 
-// Uploads the work lists of the active lattices (if they changed).
+void plan_groups(lbm_batch* b);
+
+// Uploads the work lists of the active lattices (if they changed) and plans
+// the table groups.
 lbm_status upload_list(lbm_batch* b) {
     if (!b->list_dirty) return LBM_OK;
     const int C = b->count;
@@ -1171,12 +1186,142 @@ lbm_status upload_list(lbm_batch* b) {
     b->n_active = n[2];
     b->total_chunks = (int)items[2];
     b->list_dirty = false;
+    plan_groups(b);
     return LBM_OK;
 }
 
-int kernels_per_step(const lbm_batch* b) { return (int)b->has_scheme[0] + (int)b->has_scheme[1]; }
+// A lattice's parameters with the collision constants stored once each (the
+// form of the constant-memory tables).
+lbm::KParams<float, lbm::CollConstF> kparams_table(const KParams<float>& k) {
+    lbm::KParams<float, lbm::CollConstF> t;
+    t.nx = k.nx;
+    t.ny = k.ny;
+    t.pitch = k.pitch;
+    t.plane = k.plane;
+    t.rstride = k.rstride;
+    t.px = k.px;
+    t.py = k.py;
+    t.moving = k.moving;
+    t.collide = k.collide;
+    t.raw = k.raw;
+    t.forced = k.forced;
+    t.spin_limit = k.spin_limit;
+    t.a = k.a;
+    t.iah = k.iah;
+    t.iah2 = k.iah2;
+    t.cs2 = k.cs2;
+    t.rho0 = k.rho0;
+    for (int w = 0; w < 4; ++w)
+        for (int d = 0; d < 2; ++d) t.wall_u[w][d] = k.wall_u[w][d];
+    t.lmask = k.lmask;
+    t.status = k.status;
+    t.cc = lbm::compact(k.cc);
+    return t;
+}
+
+// Which batch each device's constant-memory tables hold (by batch serial;
+// 0: none), and whether they hold its current groups.
+std::mutex g_table_mu;
+unsigned long long g_table_owner[64] = {};
+bool g_table_fresh[64] = {};
+
+// Splits the active lattices into table groups, one scheme each and at most
+// kBatchTableCap lattices each, balancing their work items (largest lattice
+// first to the lightest group); no groups when they do not fit in the
+// tables, and the shared-memory kernel steps them instead.
+void plan_groups(lbm_batch* b) {
+    const int old = b->ngroups;
+    int oraw[lbm::kBatchTables], ogrid[lbm::kBatchTables];
+    std::copy(b->graw, b->graw + lbm::kBatchTables, oraw);
+    std::copy(b->ggrid, b->ggrid + lbm::kBatchTables, ogrid);
+    b->ngroups = 0;
+    if (b->table_path && b->device >= 0 && b->device < 64) {
+        const int cap = lbm::kBatchTableCap;
+        std::vector<int> ids[2];
+        for (int k = 0; k < b->count; ++k)
+            if (b->active[k]) ids[b->p[k].scheme == 1 ? 1 : 0].push_back(k);
+        const int need0 = ((int)ids[0].size() + cap - 1) / cap;
+        const int need1 = ((int)ids[1].size() + cap - 1) / cap;
+        if (need0 + need1 <= lbm::kBatchTables) {
+            auto work = [&](int k) { return (long long)b->lat[k].nseg * b->lat[k].nbands; };
+            int g0 = 0;
+            for (int w = 0; w < 2; ++w) {
+                const int ng = w == 0 ? need0 : need1;
+                if (ng == 0) continue;
+                std::vector<int>& v = ids[w];
+                std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return work(x) > work(y); });
+                std::vector<long long> load(ng, 0);
+                for (int j = 0; j < ng; ++j) b->gtab[g0 + j].clear();
+                for (int k : v) {
+                    int best = -1;
+                    for (int j = 0; j < ng; ++j)
+                        if ((int)b->gtab[g0 + j].size() < cap && (best < 0 || load[j] < load[best]))
+                            best = j;
+                    lbm::BatchTableLattice e;
+                    e.kp = kparams_table(b->lat[k].kp);
+                    e.f[0] = b->lat[k].f[0];
+                    e.f[1] = b->lat[k].f[1];
+                    e.nseg = b->lat[k].nseg;
+                    e.nbands = b->lat[k].nbands;
+                    e.begin = (int)load[best];
+                    load[best] += work(k);
+                    b->gtab[g0 + best].push_back(e);
+                }
+                for (int j = 0; j < ng; ++j) {
+                    b->graw[g0 + j] = w;
+                    b->gtotal[g0 + j] = (int)load[j];
+                    b->ggrid[g0 + j] = lbm::batch_table_occupancy(g0 + j, b->bx) * b->sms;
+                }
+                g0 += ng;
+            }
+            b->ngroups = g0;
+        }
+    }
+    // the captured graphs hold the groups' launches: a new set of groups
+    // (not new table contents) needs new graphs
+    bool same = old == b->ngroups;
+    for (int g = 0; same && g < b->ngroups; ++g)
+        same = oraw[g] == b->graw[g] && ogrid[g] == b->ggrid[g];
+    if (!same) drop_graphs(b);
+    std::lock_guard<std::mutex> lk(g_table_mu);
+    if (b->device >= 0 && b->device < 64 && g_table_owner[b->device] == b->serial)
+        g_table_fresh[b->device] = false;
+}
+
+// Makes the device's tables hold this batch's groups.  Another batch's
+// kernels may still read them: the device is synchronised first then.
+lbm_status ensure_tables(lbm_batch* b) {
+    if (b->ngroups == 0) return LBM_OK;
+    std::lock_guard<std::mutex> lk(g_table_mu);
+    const int d = b->device;
+    if (g_table_owner[d] == b->serial && g_table_fresh[d]) return LBM_OK;
+    if (g_table_owner[d] != 0 && g_table_owner[d] != b->serial)
+        BCK(b, cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    for (int g = 0; g < b->ngroups; ++g)
+        BCK(b, lbm::batch_table_upload(g, b->gtab[g].data(), (int)b->gtab[g].size(), b->gtotal[g],
+                                       b->stream),
+            "upload of a batch lattice table");
+    g_table_owner[d] = b->serial;
+    g_table_fresh[d] = true;
+    return LBM_OK;
+}
+
+int kernels_per_step(const lbm_batch* b) {
+    return b->ngroups ? b->ngroups : (int)b->has_scheme[0] + (int)b->has_scheme[1];
+}
 
 cudaError_t launch_steps(lbm_batch* b, int n, int parity, cudaStream_t s) {
+    if (b->ngroups) {
+        // the groups one after another on s: run side by side on streams of
+        // their own they measured slower (25-31k against 38-40k MLUPS on the
+        // 512-lattice sweep), each SM then holding blocks of four modules'
+        // copies of the kernel
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; e == cudaSuccess && i < n; ++i)
+            for (int g = 0; e == cudaSuccess && g < b->ngroups; ++g)
+                e = lbm::batch_table_launch(g, (parity + i) & 1, b->bx, b->ggrid[g], b->graw[g], s);
+        return e;
+    }
     const int C = b->count;
     for (int i = 0; i < n; ++i)
         for (int w = 0; w < 2; ++w) {
@@ -1339,6 +1484,9 @@ lbm_status lbm_batch_create(const lbm_params* params, int count,
     BCKC(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev),
          "cudaDeviceGetAttribute");
     BCKC(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    b->device = dev;
+    b->serial = next_handle_serial();
+
     BCKC(lbm::dev_alloc(&b->fbase, fl * sizeof(float)), "cudaMalloc(distributions)");
     BCKC(lbm::dev_alloc(&b->mbase, ml), "cudaMalloc(link masks)");
     BCKC(lbm::dev_alloc(&b->ubase, ul * sizeof(double)), "cudaMalloc(residual fields)");
@@ -1397,6 +1545,14 @@ void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
     drop_graphs(b);
     if (b->cap) cudaStreamDestroy(b->cap);
+    {
+        // the device's tables no longer hold a live batch
+        std::lock_guard<std::mutex> lk(g_table_mu);
+        if (b->device >= 0 && b->device < 64 && g_table_owner[b->device] == b->serial) {
+            g_table_owner[b->device] = 0;
+            g_table_fresh[b->device] = false;
+        }
+    }
     cudaFree(b->fbase);
     cudaFree(b->mbase);
     cudaFree(b->ubase);
@@ -1475,10 +1631,28 @@ lbm_status lbm_batch_set_wait_limit(lbm_batch* b, int64_t polls) {
         b->geo[k].wait_limit = (unsigned)polls;
         b->lat[k].kp.spin_limit = (unsigned)polls;
     }
+    b->list_dirty = true;  // the lattice tables carry the limit too
     BCK(b, cudaMemcpyAsync(b->d_lat, b->lat.data(), sizeof(BatchLattice<float>) * b->count,
                            cudaMemcpyHostToDevice, b->stream),
         "cudaMemcpyAsync(lattice table)");
     return LBM_OK;
+}
+
+lbm_status lbm_batch_set_table_path(lbm_batch* b, int enable) {
+    if (!b) return LBM_ERR_INVALID;
+    if (enable != 0 && enable != 1) {
+        bset_err(b, "enable must be 0 or 1");
+        return LBM_ERR_INVALID;
+    }
+    b->table_path = enable != 0;
+    b->list_dirty = true;
+    return LBM_OK;
+}
+
+int lbm_batch_table_groups(lbm_batch* b) {
+    if (!b) return -1;
+    if (upload_list(b) != LBM_OK) return -1;
+    return b->ngroups;
 }
 
 lbm_status lbm_batch_get_shape(const lbm_batch* b, int* block_x, int* rows_per_band) {
@@ -1496,6 +1670,7 @@ namespace {
 lbm_status advance(lbm_batch* b, int64_t nsteps, bool graphs) {
     if (lbm_status s = upload_list(b); s != LBM_OK) return s;
     if (b->n_active == 0 || nsteps == 0) return LBM_OK;
+    if (lbm_status s = ensure_tables(b); s != LBM_OK) return s;
     int64_t left = nsteps;
     while (graphs && left >= kGraphSteps) {
         if (lbm_status s = ensure_graph(b, b->parity); s != LBM_OK) return s;

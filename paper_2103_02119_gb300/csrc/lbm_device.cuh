@@ -34,26 +34,72 @@ template <typename T> struct Lane;
 template <> struct Lane<float> { using V = float2; };
 template <> struct Lane<double> { using V = double; };
 
-// Constants of the collision, each held as a lane value (FP32: the same
-// value in both halves of a float2), computed once on the host.
+// Constants of the collision (the field list, in storage order):
+//   rho0, -rho0, a, a^2, cs2, cs2^2;
+//   force, half force, twice the force (x and y);
+//   1/2, 2, 3/2, -3/2;
+//   the rho-free, u-free parts of B1, B2, C1, C2 (Eq. 40);
+//   (1 - 3cs2)/2, (a^2 - 3cs2)/2 (strain solve);
+//   iso (1 - 3cs2), iso (a^2 - 3cs2), -3 gi;
+//   1 - w_j/2 and -w_j for j = 3..8;
+//   1/(2a), -1/(2a), 1/(2a^2), -1/a^2 and the halves of the first three;
+//   the halves of 1 - w_j/2 and -w_j for j = 3, 4.
+#define LBM_COLL_FIELDS(X)                                                              \
+    X(rho0) X(nrho0) X(a) X(a2) X(cs2) X(cs4)                                          \
+    X(Fx) X(Fy) X(hFx) X(hFy) X(twoFx) X(twoFy)                                        \
+    X(half) X(two) X(c15) X(nc15)                                                      \
+    X(b1c) X(b2c) X(c1c) X(c2c)                                                        \
+    X(g1h) X(g2h)                                                                      \
+    X(g1i) X(g2i) X(ng3)                                                               \
+    X(lw3) X(lw4) X(lw5) X(lw6) X(lw7) X(lw8)                                          \
+    X(nw3) X(nw4) X(nw5) X(nw6) X(nw7) X(nw8)                                          \
+    X(iah) X(niah) X(iah2) X(nia2)                                                     \
+    X(qa) X(nqa) X(qa2)                                                                \
+    X(lw3h) X(lw4h) X(nw3h) X(nw4h)
+
+// The constants as lane values (FP32: the same value in both halves of a
+// float2), computed once on the host; the form the collision takes.
 template <typename T>
 struct CollConst {
     using V = typename Lane<T>::V;
-    V rho0, nrho0, a, a2, cs2, cs4;
-    V Fx, Fy, hFx, hFy, twoFx, twoFy;  // force, half force, twice the force
-    V half, two, c15, nc15;            // 1/2, 2, 3/2, -3/2
-    V b1c, b2c, c1c, c2c;              // rho-free, u-free parts of B1, B2, C1, C2 (Eq. 40)
-    V g1h, g2h;                        // (1 - 3cs2)/2, (a^2 - 3cs2)/2 (strain solve)
-    V g1i, g2i, ng3;                   // iso (1 - 3cs2), iso (a^2 - 3cs2), -3 gi
-    V lw3, lw4, lw5, lw6, lw7, lw8;    // 1 - w_j/2
-    V nw3, nw4, nw5, nw6, nw7, nw8;    // -w_j
-    V iah, niah, iah2, nia2;           // 1/(2a), -1/(2a), 1/(2a^2), -1/a^2
-    V qa, nqa, qa2;                    // halves of iah, niah, iah2
-    V lw3h, lw4h, nw3h, nw4h;          // halves of lw3, lw4, nw3, nw4
+#define LBM_DECL_LANE(n) V n;
+    LBM_COLL_FIELDS(LBM_DECL_LANE)
+#undef LBM_DECL_LANE
 };
 
-// Kernel parameters, converted once on the host to the arithmetic type T.
+// The same constants stored once each (FP32), half the size: the form a
+// batch keeps in its constant-memory lattice table.
+struct CollConstF {
+#define LBM_DECL_ONE(n) float n;
+    LBM_COLL_FIELDS(LBM_DECL_ONE)
+#undef LBM_DECL_ONE
+};
+
+// Either form as lane values for the collision, as a copy (bound to the
+// parameter block by reference, the FP32 step spills a word and ran 1.5 %
+// slower).
 template <typename T>
+__host__ __device__ __forceinline__ CollConst<T> to_lanes(const CollConst<T>& c) {
+    return c;
+}
+__host__ __device__ __forceinline__ CollConst<float> to_lanes(const CollConstF& c) {
+    CollConst<float> l;
+#define LBM_COPY_LANE(n) l.n = make_float2(c.n, c.n);
+    LBM_COLL_FIELDS(LBM_COPY_LANE)
+#undef LBM_COPY_LANE
+    return l;
+}
+__host__ __device__ __forceinline__ CollConstF compact(const CollConst<float>& c) {
+    CollConstF o;
+#define LBM_COPY_ONE(n) o.n = c.n.x;
+    LBM_COLL_FIELDS(LBM_COPY_ONE)
+#undef LBM_COPY_ONE
+    return o;
+}
+
+// Kernel parameters, converted once on the host to the arithmetic type T;
+// CC: the form of the collision constants.
+template <typename T, typename CC = CollConst<T>>
 struct KParams {
     int nx, ny, pitch;        // pitch: padded row length (also of the link mask)
     long long plane;          // element stride between population planes
@@ -68,7 +114,7 @@ struct KParams {
     T wall_u[4][2];
     const uint8_t* __restrict__ lmask;  // per-cell link mask (nullable)
     int* status;                        // bit 0: a bounded wait ran out
-    CollConst<T> cc;                    // constants of the collision
+    CC cc;                              // constants of the collision
 };
 
 // Host/device double-precision parameters for the auxiliary kernels.
@@ -513,9 +559,8 @@ __device__ __forceinline__ typename Lane<T>::V collide_raw(const CollConst<T>& c
 // of a boundary cell whose link k points into a moving wall node:
 // f~_k -= (f^eq_k - f^eq_opp(k))(rho_w, U_w), rho_w the cell's density.
 // Nodes outside the domain in both x and y belong to the bottom/top wall.
-template <typename T>
-__device__ __forceinline__ void moving_wall(const KParams<T>& p, int x, int y, T rho,
-                                            T f[9]) {
+template <typename T, typename P>
+__device__ __forceinline__ void moving_wall(const P& p, int x, int y, T rho, T f[9]) {
 #pragma unroll
     for (int k = 1; k < 9; ++k) {
         const int tx = x + ex(k), ty = y + ey(k);

@@ -71,6 +71,56 @@ cudaError_t launch_batch_step(const BatchLattice<T>* lat, const int* active, con
 template <typename T>
 int batch_occupancy(int bx);
 
+// One lattice of a group of a batch, in a constant-memory table
+// (batch_table.cuh): its parameters with the collision constants stored once
+// each, its buffers and its work items (nseg * nbands, in the group's list
+// from `begin` on, which the table keeps in an array of its own).
+struct BatchTableLattice {
+    KParams<float, CollConstF> kp;
+    float* f[2];
+    int nseg, nbands;
+    int begin;  // host side only
+};
+// Tables (translation units rc_batch_t0.cu ..), and lattices per table: a
+// module's constant bank holds 64 KiB.
+constexpr int kBatchTables = 4;
+constexpr int kBatchTableCap = 60000 / (int)sizeof(BatchTableLattice);
+#define LBM_DECLARE_BATCH_TABLE(S)                                                         \
+    cudaError_t batch_table_upload_##S(const BatchTableLattice* lat, int n, int total,      \
+                                       cudaStream_t s);                                     \
+    cudaError_t batch_table_launch_##S(int parity, int bx, int grid, int raw, cudaStream_t s); \
+    int batch_table_occupancy_##S(int bx);
+LBM_DECLARE_BATCH_TABLE(0)
+LBM_DECLARE_BATCH_TABLE(1)
+LBM_DECLARE_BATCH_TABLE(2)
+LBM_DECLARE_BATCH_TABLE(3)
+#undef LBM_DECLARE_BATCH_TABLE
+// Table `slot`: copy n lattices (host array) with `total` work items into it,
+// asynchronously on s (after the kernels of the slot that were issued before
+// on s; the caller orders them).
+inline cudaError_t batch_table_upload(int slot, const BatchTableLattice* lat, int n, int total,
+                                      cudaStream_t s) {
+    return slot == 0   ? batch_table_upload_0(lat, n, total, s)
+           : slot == 1 ? batch_table_upload_1(lat, n, total, s)
+           : slot == 2 ? batch_table_upload_2(lat, n, total, s)
+                       : batch_table_upload_3(lat, n, total, s);
+}
+// One step of every lattice of table `slot` (all of one scheme: raw = 1 for
+// RNR-LBM), from buffer f[parity], on a persistent grid of `grid` blocks.
+inline cudaError_t batch_table_launch(int slot, int parity, int bx, int grid, int raw,
+                                      cudaStream_t s) {
+    return slot == 0   ? batch_table_launch_0(parity, bx, grid, raw, s)
+           : slot == 1 ? batch_table_launch_1(parity, bx, grid, raw, s)
+           : slot == 2 ? batch_table_launch_2(parity, bx, grid, raw, s)
+                       : batch_table_launch_3(parity, bx, grid, raw, s);
+}
+inline int batch_table_occupancy(int slot, int bx) {
+    return slot == 0   ? batch_table_occupancy_0(bx)
+           : slot == 1 ? batch_table_occupancy_1(bx)
+           : slot == 2 ? batch_table_occupancy_2(bx)
+                       : batch_table_occupancy_3(bx);
+}
+
 // One lattice of a batch, as the batch residual kernels see it.
 struct BatchAux {
     AuxParams a;      // a.lmask always set

@@ -116,6 +116,8 @@ def _load():
     L.lbm_batch_is_active.argtypes = [_P, ctypes.c_int]
     L.lbm_batch_set_shape.argtypes = [_P, ctypes.c_int, ctypes.c_int]
     L.lbm_batch_set_wait_limit.argtypes = [_P, ctypes.c_int64]
+    L.lbm_batch_set_table_path.argtypes = [_P, ctypes.c_int]
+    L.lbm_batch_table_groups.argtypes = [_P]
     _IP = ctypes.POINTER(ctypes.c_int)
     L.lbm_batch_get_shape.argtypes = [_P, _IP, _IP]
     L.lbm_batch_tune.argtypes = [_P, ctypes.c_int, _IP, _IP]
@@ -453,6 +455,14 @@ def lbm_batch_set_wait_limit(b, polls: int):
     _bcheck(lib.lbm_batch_set_wait_limit(b, int(polls)), b)
 
 
+def lbm_batch_set_table_path(b, enable: bool):
+    _bcheck(lib.lbm_batch_set_table_path(b, int(enable)), b)
+
+
+def lbm_batch_table_groups(b) -> int:
+    return lib.lbm_batch_table_groups(b)
+
+
 def lbm_batch_get_shape(b):
     bx, rows = ctypes.c_int(), ctypes.c_int()
     _bcheck(lib.lbm_batch_get_shape(b, ctypes.byref(bx), ctypes.byref(rows)), b)
@@ -660,6 +670,13 @@ class Batch:
 
     def is_active(self, k) -> bool:
         return lbm_batch_is_active(self.b, k) == 1
+
+    def set_table_path(self, enable):
+        lbm_batch_set_table_path(self.b, enable)
+
+    @property
+    def table_groups(self) -> int:
+        return lbm_batch_table_groups(self.b)
 
     def set_shape(self, block_x, rows_per_band):
         lbm_batch_set_shape(self.b, block_x, rows_per_band)

@@ -59,9 +59,14 @@ def ws():
     return uneven_set()
 
 
-def test_batch_matches_single_handles_bit_for_bit(ws):
+@pytest.mark.parametrize("table", [True, False])
+def test_batch_matches_single_handles_bit_for_bit(ws, table):
+    """Either parameter path: the constant-memory tables (one group here) or
+    the global table."""
     from paper_2103_02119_gb300.lbm import Batch
     b = Batch(ws)
+    b.set_table_path(table)
+    assert b.table_groups == (1 if table else 0)
     ref = singles(ws)
     for n in (1, 2, 57, 120):        # direct launches and graph replays, both parities
         b.step(n)
@@ -102,9 +107,11 @@ def test_batch_lattice_matches_oracle(orc, ws):
         assert rel_l2(np.stack([ug, vg]), np.stack([uo, vo])) <= F32_RTOL_U
 
 
-def test_retire_and_reactivate(ws):
+@pytest.mark.parametrize("table", [True, False])
+def test_retire_and_reactivate(ws, table):
     from paper_2103_02119_gb300.lbm import Batch
     b = Batch(ws)
+    b.set_table_path(table)
     ref = singles(ws)
     b.step(3)
     for lat in ref:
@@ -132,6 +139,72 @@ def test_retire_and_reactivate(ws):
     before = b.launch_count
     b.step(10)
     assert b.launch_count == before
+
+
+def _many(count, seed):
+    """`count` small lattices of both schemes, ragged sizes, masks."""
+    rng = np.random.default_rng(seed)
+    ws, schemes = [], []
+    for k in range(count):
+        nx, ny = int(rng.integers(5, 40)), int(rng.integers(4, 30))
+        if k % 2:
+            w = _fields(W.cavity(nx, ny, 0.5, 0.075, 0.04, 100.0), 100 + k)
+        else:
+            w = W.taylor_green(nx, ny, 0.8, 0.19, 0.02, u0=0.02, seed=k).with_(
+                mask=W.random_obstacles(nx, ny, seed=k, coverage=0.05))
+        ws.append(w)
+        schemes.append(1 if k % 3 == 0 else 0)
+    return ws, schemes
+
+
+@pytest.mark.parametrize("count,groups", [(400, 3), (900, 0)])
+def test_table_groups_and_fallback(count, groups):
+    """400 lattices (266 RC-LBM, 134 RNR-LBM) fill three constant-memory
+    tables (at most 170 lattices each, one scheme each); 900 would need six
+    of the four and step from the global table.  Either way a sample of lattices equals single-lattice
+    handles bit for bit, across graph replays and a retirement that changes
+    the groups."""
+    from paper_2103_02119_gb300.lbm import Batch, Lattice
+    ws, schemes = _many(count, count)
+    b = Batch(ws, schemes=schemes)
+    assert b.table_groups == groups
+    sample = list(range(0, count, 37)) + [count - 1]
+    ref = []
+    for k in sample:
+        w = ws[k] if ws[k].mask is not None else ws[k].with_(
+            mask=np.zeros((ws[k].ny, ws[k].nx), np.uint8))
+        ref.append(Lattice.from_workload(w, precision=32, scheme=schemes[k]))
+    b.step(57)
+    for lat in ref:
+        lat.step(57)
+    for j, k in enumerate(sample):
+        same_state(b, k, ref[j])
+    # retire every third lattice: new groups, new graphs, same results
+    for k in range(0, count, 3):
+        if k not in sample:
+            b.set_active(k, False)
+    b.step(50)
+    for lat in ref:
+        lat.step(50)
+    for j, k in enumerate(sample):
+        same_state(b, k, ref[j])
+
+
+def test_two_batches_share_the_tables(ws):
+    """Two batches on one device take turns with the constant-memory tables:
+    each re-uploads its own before it steps."""
+    from paper_2103_02119_gb300.lbm import Batch
+    a, c = Batch(ws), Batch(ws[::-1])
+    ra, rc = singles(ws), singles(ws[::-1])
+    for n in (3, 50, 7):
+        a.step(n)
+        c.step(n)
+        for lat in ra + rc:
+            lat.step(n)
+    for k in range(len(ws)):
+        same_state(a, k, ra[k])
+        same_state(c, k, rc[k])
+    assert a.table_groups == 1 and c.table_groups == 1
 
 
 def test_residuals_match_single_diagnostics(ws):
@@ -224,4 +297,6 @@ def test_batch_errors():
         b.set_shape(32, 0)
     with pytest.raises(LbmError):
         b.step(-1)
+    with pytest.raises(LbmError):
+        L.lbm_batch_set_table_path(b.b, 2)
     assert b.shape == (32, 16)
