@@ -452,8 +452,23 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
 #pragma unroll
         for (int j = 0; j < VC; ++j) gp[i][j] = T(0);
 
+    // With a mask the halo lanes' link bits are a global read: each row's
+    // are loaded one row ahead, so that the read's latency does not sit
+    // before the row barrier.
+    auto halo_bits = [&](int k) -> unsigned {
+        const int r = rfirst + dir * k;
+        if (!(MASK && hpull && k < nit && row_valid(r))) return 0xFFu;
+        return bits_at(hx, wrap_row(r));
+    };
+    unsigned hb_next = MASK ? halo_bits(0) : 0u;
+
     for (int k = 0; k < nit; ++k) {
         const int r = rfirst + dir * k;
+        unsigned hb_cur = 0u;
+        if constexpr (MASK) {
+            hb_cur = hb_next;
+            hb_next = halo_bits(k + 1);
+        }
         const int s = k % kStages;
         const int slot = k & 3;
         const bool to = !mbar_wait(bar0 + 8u * s, (unsigned)((k / kStages) & 1), p.spin_limit);
@@ -508,7 +523,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
         if (tx < 32) {
             T h = T(0);
             if (!to && rv && hpull) {
-                const unsigned hb = bits_at(hx, rr);
+                const unsigned hb = MASK ? hb_cur : bits_at(hx, rr);
                 if (hb != 0xFFu) {
                     const int i = hi;
                     if (hb == 0u && !hwrap) {
