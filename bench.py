@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--warm-only", action="store_true",
                     help="print only the warm-start measurement")
     ap.add_argument("--warm-epochs", type=int, default=40)
+    ap.add_argument("--warm-coarse", type=int, default=1,
+                    help="network grid this many times coarser than the instances "
+                         "(predictions prolonged on the GPU)")
     ap.add_argument("--nn-only", action="store_true",
                     help="only the surrogate's forward and training-step times")
     ap.add_argument("--nn-prof", action="store_true",
@@ -531,25 +534,27 @@ def small_lattice(torch):
 
 # ---------------------------------------------------------------- warm start --
 
-def warm_start_measure(torch, ntrain, epochs, n=32, ntest=32):
+def warm_start_measure(torch, ntrain, epochs, n=32, ntest=32, coarse=1):
     """Trains the surrogate on steady cavities from the batched solver, then
     runs held-out instances to R <= 1e-8 from the rest state and from the
-    network's prediction (both as one batch each)."""
+    network's prediction (both as one batch each).  coarse > 1: the network
+    works on a grid that many times coarser (block-averaged inputs and
+    targets) and its predictions are prolonged to the instances' grid."""
     import numpy as np
     from paper_2103_02119_gb300 import warmstart as WS
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     wls, x, t, fl, _ = WS.build_dataset(ntrain, seed=0, n=n, stream=stream)
     t_data = time.perf_counter() - t0
-    ws = WS.WarmStart([32, 64, 128, 256], n=n, max_batch=32, seed=0, stream=stream)
+    ws = WS.WarmStart([32, 64, 128, 256], n=n // coarse, max_batch=32, seed=0, stream=stream)
     t0 = time.perf_counter()
-    hist = ws.train(x, t, fl, epochs=epochs, lr=2e-3, lr_final=2e-4)
+    hist = ws.train(*WS.coarsen(x, t, fl, coarse), epochs=epochs, lr=2e-3, lr_final=2e-4)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     test = WS.cavity_set(ntest, seed=1, n=n)
     tx = WS.inputs_of(test)
     t0 = time.perf_counter()
-    y = ws.predict(tx)
+    y = ws.predict_fine(tx, WS.fluid_of(test), coarse)
     t_pred = time.perf_counter() - t0
     rest = WS.solve(test, stream=stream)
     warm = WS.solve(test, inits=[WS.fields_of(w, y[k]) for k, w in enumerate(test)],
@@ -567,7 +572,9 @@ def warm_start_measure(torch, ntrain, epochs, n=32, ntest=32):
     ratio = warm["steps"][ok] / np.maximum(rest["steps"][ok], 1)
     return {"instances": f"{n}x{n} lid-driven cavities with obstacles, a in [0.5, 1], "
                          "Re in [20, 200], seeded; train seed 0, test seed 1",
-            "network": "4-level conv encoder-decoder, 32-256 channels, BF16 tcgen05 (TMEM accumulator)",
+            "network": "4-level conv encoder-decoder, 32-256 channels, BF16 tcgen05 (TMEM accumulator)"
+                       + (f", on a {n // coarse}x{n // coarse} grid, predictions prolonged x{coarse}"
+                          if coarse > 1 else ""),
             "train_instances": len(wls), "epochs": epochs, "final_train_loss": hist[-1],
             "test_instances": ntest, "test_rms_error": rms,
             "data_seconds": t_data, "train_seconds": t_train,
@@ -661,7 +668,8 @@ def main():
     if args.warm_only:
         if rank == 0:
             print(json.dumps(warm_start_measure(torch, args.warm_train, args.warm_epochs,
-                                                n=args.warm_n, ntest=args.warm_test)), flush=True)
+                                                n=args.warm_n, ntest=args.warm_test,
+                                                coarse=args.warm_coarse)), flush=True)
         return
     if args.nn_only:
         if rank == 0:
@@ -759,7 +767,7 @@ def main():
     warm = None
     if rank == 0 and not args.no_warm:
         warm = warm_start_measure(torch, args.warm_train, args.warm_epochs, n=args.warm_n,
-                                  ntest=args.warm_test)
+                                  ntest=args.warm_test, coarse=args.warm_coarse)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -81,6 +81,22 @@ lbm_status lbm_nn_set_params(lbm_nn* nn, const float* params);
  * host arrays, 1 <= n <= max_batch. */
 lbm_status lbm_nn_forward(lbm_nn* nn, const float* x, int n, float* y);
 
+/* Prolongation of outputs to a grid `factor` (1 .. 16) times finer, for
+ * instances larger than the network's grid: y (n x height x width x 3
+ * floats, e.g. lbm_nn_forward's output on block-averaged inputs) is
+ * interpolated bilinearly between cell centres (the centre of fine cell
+ * (Y, X) at coarse coordinates ((Y + 1/2) / factor - 1/2, ...), clamped to
+ * the outermost coarse centres), set to 0 on the solid fine cells, and put
+ * through the fixed output stage at the fine resolution with the fine
+ * fluid flags (fluid: n x H x W bytes, nonzero = fluid, H = factor x
+ * height, W = factor x width), so that the result carries no staggered
+ * momentum on the fine lattice either.  out: n x H x W x 3 floats.  Host
+ * arrays, 1 <= n <= max_batch; the fine buffers are allocated on the first
+ * call at a size and kept until lbm_nn_destroy.  Errors: LBM_ERR_INVALID,
+ * LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_nn_prolong(lbm_nn* nn, const float* y, int n, int factor, const uint8_t* fluid,
+                          float* out);
+
 /* Loss and parameter gradients (param_count floats, nullable) of a batch:
  * x as above, target n x height x width x 3, fluid n x height x width
  * bytes.  Does not change the parameters. */

@@ -152,6 +152,37 @@ def output_stage_backward(g, fluid):
     return smooth(unstagger(g, fluid), fluid)
 
 
+def prolong(y, factor, fluid):
+    """Bilinear interpolation of cell-centred fields y (n, h, w, c) onto a
+    grid `factor` times finer: the centre of fine cell (Y, X) sits at coarse
+    coordinates ((Y + 1/2) / factor - 1/2, (X + 1/2) / factor - 1/2), clamped
+    to [0, h - 1] x [0, w - 1] (constant beyond the outermost coarse
+    centres); fine cells where `fluid` (n, h factor, w factor) is false get
+    0.  Written cell by cell from the definition."""
+    y = np.asarray(y, dtype=np.float64)
+    n, h, w, c = y.shape
+    H, W = h * factor, w * factor
+    out = np.zeros((n, H, W, c))
+    for Y in range(H):
+        yc = min(max((Y + 0.5) / factor - 0.5, 0.0), h - 1.0)
+        y0 = int(np.floor(yc))
+        y1 = min(y0 + 1, h - 1)
+        ty = yc - y0
+        for X in range(W):
+            xc = min(max((X + 0.5) / factor - 0.5, 0.0), w - 1.0)
+            x0 = int(np.floor(xc))
+            x1 = min(x0 + 1, w - 1)
+            tx = xc - x0
+            out[:, Y, X] = ((1 - ty) * ((1 - tx) * y[:, y0, x0] + tx * y[:, y0, x1])
+                            + ty * ((1 - tx) * y[:, y1, x0] + tx * y[:, y1, x1]))
+    return out * np.asarray(fluid, dtype=np.float64)[..., None]
+
+
+def prolong_stage(y, factor, fluid):
+    """prolong() followed by the output stage on the fine grid."""
+    return output_stage(prolong(y, factor, fluid), fluid)
+
+
 def layer_shapes(channels, cin=4, cout=3):
     """(cin, cout) of the convolutions, in the order of the forward pass."""
     L = len(channels)

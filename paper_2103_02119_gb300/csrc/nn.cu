@@ -601,15 +601,25 @@ __device__ __forceinline__ V block_sum(V v) {
 //            projection on (-1)^y, over the fluid cells of each instance
 // Both are self-adjoint: the backward pass applies unstagger, then smooth.
 
-__device__ __forceinline__ bool fluid_at(const bf16* xin, int xcp, long long p) {
-    return __bfloat162float(xin[p * xcp]) < 0.5f;
-}
+// Fluid flags: the network input's channel 0 (the solid flag) below 1/2, or
+// a byte per cell (nonzero: fluid).
+struct FluidIn {
+    const bf16* x;
+    int cp;
+    __device__ __forceinline__ bool operator()(long long p) const {
+        return __bfloat162float(x[p * cp]) < 0.5f;
+    }
+};
+struct FluidBytes {
+    const uint8_t* m;
+    __device__ __forceinline__ bool operator()(long long p) const { return m[p] != 0; }
+};
 
 // in: bf16 [P][icp] or float [P][3]; out: float [P][3] or bf16 [P][ocp] (the
 // channels past 3 zeroed)
-template <bool IN_BF16, bool OUT_BF16>
-__global__ void out_smooth_kernel(const void* in, int icp, const bf16* xin, int xcp, void* out,
-                                  int ocp, int n, int h, int w) {
+template <bool IN_BF16, bool OUT_BF16, typename FL>
+__global__ void out_smooth_kernel(const void* in, int icp, FL fluid, void* out, int ocp, int n,
+                                  int h, int w) {
     const long long P = (long long)n * h * w;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
          p += (long long)gridDim.x * blockDim.x) {
@@ -618,7 +628,7 @@ __global__ void out_smooth_kernel(const void* in, int icp, const bf16* xin, int 
         const int y = (int)(r % h);
         const long long base = r / h * h;
         float acc[3] = {0.0f, 0.0f, 0.0f};
-        if (fluid_at(xin, xcp, p)) {
+        if (fluid(p)) {
             for (int dy = -1; dy <= 1; ++dy) {
                 const int yy = y + dy;
                 if (yy < 0 || yy >= h) continue;
@@ -626,7 +636,7 @@ __global__ void out_smooth_kernel(const void* in, int icp, const bf16* xin, int 
                     const int xx = x + dx;
                     if (xx < 0 || xx >= w) continue;
                     const long long q = (base + yy) * w + xx;
-                    if (!fluid_at(xin, xcp, q)) continue;
+                    if (!fluid(q)) continue;
                     const float wt = (dy == 0 ? 0.5f : 0.25f) * (dx == 0 ? 0.5f : 0.25f);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
@@ -651,14 +661,14 @@ __global__ void out_smooth_kernel(const void* in, int icp, const bf16* xin, int 
 
 // Block k: sums over the fluid cells of instance k of (-1)^x v1, (-1)^y v2 and
 // the cell count, in a fixed order.
-__global__ void __launch_bounds__(kThreads) stagger_sum_kernel(const float* v, const bf16* xin,
-                                                               int xcp, double* sums, int h,
-                                                               int w) {
+template <typename FL>
+__global__ void __launch_bounds__(kThreads) stagger_sum_kernel(const float* v, FL fluid,
+                                                               double* sums, int h, int w) {
     const long long hw = (long long)h * w, p0 = (long long)blockIdx.x * hw;
     double s1 = 0.0, s2 = 0.0, nf = 0.0;
     for (long long i = threadIdx.x; i < hw; i += blockDim.x) {
         const long long p = p0 + i;
-        if (!fluid_at(xin, xcp, p)) continue;
+        if (!fluid(p)) continue;
         const int x = (int)(i % w), y = (int)(i / w);
         s1 += (x & 1) ? -(double)v[p * 3 + 1] : (double)v[p * 3 + 1];
         s2 += (y & 1) ? -(double)v[p * 3 + 2] : (double)v[p * 3 + 2];
@@ -674,8 +684,9 @@ __global__ void __launch_bounds__(kThreads) stagger_sum_kernel(const float* v, c
     }
 }
 
-__global__ void stagger_apply_kernel(const float* v, const bf16* xin, int xcp,
-                                     const double* sums, float* out, long long P, int h, int w) {
+template <typename FL>
+__global__ void stagger_apply_kernel(const float* v, FL fluid, const double* sums, float* out,
+                                     long long P, int h, int w) {
     const long long hw = (long long)h * w;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
          p += (long long)gridDim.x * blockDim.x) {
@@ -683,7 +694,7 @@ __global__ void stagger_apply_kernel(const float* v, const bf16* xin, int xcp,
         const int x = (int)(i % w), y = (int)(i / w);
         float o1 = v[p * 3 + 1], o2 = v[p * 3 + 2];
         const double nf = sums[3 * k + 2];
-        if (nf > 0.0 && fluid_at(xin, xcp, p)) {
+        if (nf > 0.0 && fluid(p)) {
             const float c1 = (float)(sums[3 * k] / nf), c2 = (float)(sums[3 * k + 1] / nf);
             o1 -= (x & 1) ? -c1 : c1;
             o2 -= (y & 1) ? -c2 : c2;
@@ -691,6 +702,44 @@ __global__ void stagger_apply_kernel(const float* v, const bf16* xin, int xcp,
         out[p * 3] = v[p * 3];
         out[p * 3 + 1] = o1;
         out[p * 3 + 2] = o2;
+    }
+}
+
+// Bilinear prolongation by an integer factor f of cell-centred fields:
+// coarse [n][hc][wc][3] -> fine [n][hc f][wc f][3].  The centre of fine cell
+// (Y, X) lies at coarse coordinates ((Y + 1/2) / f - 1/2, (X + 1/2) / f - 1/2),
+// clamped to the coarse cell centres (constant beyond the outermost ones);
+// solid fine cells get 0.
+__global__ void prolong_kernel(const float* in, const uint8_t* fluid, float* out, int n, int hc,
+                               int wc, int f) {
+    const int H = hc * f, W = wc * f;
+    const long long P = (long long)n * H * W;
+    const float inv = 1.0f / (float)f;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(p % W);
+        const long long r = p / W;
+        const int Y = (int)(r % H);
+        const long long k = r / H;
+        float* o = out + p * 3;
+        if (!fluid[p]) {
+            o[0] = o[1] = o[2] = 0.0f;
+            continue;
+        }
+        const float yc = fminf(fmaxf(((float)Y + 0.5f) * inv - 0.5f, 0.0f), (float)(hc - 1));
+        const float xc = fminf(fmaxf(((float)X + 0.5f) * inv - 0.5f, 0.0f), (float)(wc - 1));
+        const int y0 = (int)yc, x0 = (int)xc;
+        const int y1 = min(y0 + 1, hc - 1), x1 = min(x0 + 1, wc - 1);
+        const float ty = yc - (float)y0, tx = xc - (float)x0;
+        const float* a = in + k * hc * wc * 3;
+        const float* r0 = a + (long long)y0 * wc * 3;
+        const float* r1 = a + (long long)y1 * wc * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float lo = fmaf(tx, r0[x1 * 3 + c] - r0[x0 * 3 + c], r0[x0 * 3 + c]);
+            const float hi = fmaf(tx, r1[x1 * 3 + c] - r1[x0 * 3 + c], r1[x0 * 3 + c]);
+            o[c] = fmaf(ty, hi - lo, lo);
+        }
     }
 }
 
@@ -824,6 +873,9 @@ struct lbm_nn {
     float* gout = nullptr;     // the loss gradient of yout [P][3]
     float* tmp3 = nullptr;     // the output stage's intermediate [P][3]
     double* ssum = nullptr;    // per instance: the staggered sums and fluid count
+    float* fine = nullptr;     // lbm_nn_prolong: two fine fields [max_batch][H f][W f][3]
+    uint8_t* fine_fl = nullptr;  // and their fluid flags
+    long long fine_cells = 0;  // cells per fine field the buffers hold
     int* gemm_err = nullptr;   // set by a GEMM whose bounded wait ran out
     long long adam_t = 0;
     int64_t launches = 0;
@@ -949,10 +1001,11 @@ lbm_status upload_inputs(lbm_nn* nn, const float* x, const float* tgt, const uin
 lbm_status unstagger(lbm_nn* nn, int n, const float* v, float* out) {
     const lbm_nn::Tensor& X = nn->t[nn->x_id];
     const long long P = pixels(nn, nn->x_id, n);
-    stagger_sum_kernel<<<n, kThreads, 0, nn->stream>>>(v, X.v, X.cp, nn->ssum, X.h, X.w);
+    const FluidIn fl{X.v, X.cp};
+    stagger_sum_kernel<<<n, kThreads, 0, nn->stream>>>(v, fl, nn->ssum, X.h, X.w);
     NCK(nn, cudaGetLastError(), "staggered sums");
-    stagger_apply_kernel<<<grid_of(P), kThreads, 0, nn->stream>>>(v, X.v, X.cp, nn->ssum, out, P,
-                                                                  X.h, X.w);
+    stagger_apply_kernel<<<grid_of(P), kThreads, 0, nn->stream>>>(v, fl, nn->ssum, out, P, X.h,
+                                                                  X.w);
     NCK(nn, cudaGetLastError(), "staggered projection");
     nn->launches += 3;  // with the smoothing launched beside it
     return LBM_OK;
@@ -999,8 +1052,8 @@ lbm_status forward(lbm_nn* nn, int n) {
     const lbm_nn::Tensor& X = nn->t[nn->x_id];
     const lbm_nn::Tensor& Y = nn->t[nn->y_id];
     const long long P = pixels(nn, nn->y_id, n);
-    out_smooth_kernel<true, false><<<grid_of(P), kThreads, 0, s>>>(Y.v, Y.cp, X.v, X.cp, nn->tmp3,
-                                                                   3, n, Y.h, Y.w);
+    out_smooth_kernel<true, false><<<grid_of(P), kThreads, 0, s>>>(
+        Y.v, Y.cp, FluidIn{X.v, X.cp}, nn->tmp3, 3, n, Y.h, Y.w);
     NCK(nn, cudaGetLastError(), "output smoothing");
     return unstagger(nn, n, nn->tmp3, nn->yout);
 }
@@ -1031,7 +1084,7 @@ lbm_status backward(lbm_nn* nn, int n, float* loss) {
     // the output stage backward: unstagger, then smooth into the gradient of
     // the last convolution's output (BF16, padded channels zeroed)
     if (lbm_status st = unstagger(nn, n, nn->gout, nn->tmp3); st != LBM_OK) return st;
-    out_smooth_kernel<false, true><<<grid_of(P), kThreads, 0, s>>>(nn->tmp3, 3, X.v, X.cp,
+    out_smooth_kernel<false, true><<<grid_of(P), kThreads, 0, s>>>(nn->tmp3, 3, FluidIn{X.v, X.cp},
                                                                    G[nn->y_id], Y.cp, n, Y.h, Y.w);
     NCK(nn, cudaGetLastError(), "output smoothing (backward)");
     std::vector<char> pool_seen(nn->t.size(), 0);
@@ -1280,6 +1333,8 @@ void lbm_nn_destroy(lbm_nn* nn) {
     cudaFree(nn->tmp3);
     cudaFree(nn->ssum);
     cudaFree(nn->gemm_err);
+    cudaFree(nn->fine);
+    cudaFree(nn->fine_fl);
     delete nn;
 }
 
@@ -1370,6 +1425,56 @@ lbm_status lbm_nn_forward(lbm_nn* nn, const float* x, int n, float* y) {
         "cudaMemcpyAsync(D2H)");
     NCK(nn, cudaStreamSynchronize(nn->stream), "cudaStreamSynchronize");
     return check_gemm(nn);
+}
+
+lbm_status lbm_nn_prolong(lbm_nn* nn, const float* y, int n, int factor, const uint8_t* fluid,
+                          float* out) {
+    LBM_RANGE("lbm_nn_prolong");
+    if (!nn || !y || !fluid || !out) return LBM_ERR_INVALID;
+    if (bad_batch(nn, n)) return LBM_ERR_INVALID;
+    if (factor < 1 || factor > 16) {
+        nn_err(nn, "factor %d outside [1, 16]", factor);
+        return LBM_ERR_INVALID;
+    }
+    const int H = nn->H * factor, W = nn->W * factor;
+    const long long cells = (long long)H * W;
+    const cudaStream_t s = nn->stream;
+    if (cells > nn->fine_cells) {
+        // grown on demand, kept until the network is destroyed
+        NCK(nn, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        cudaFree(nn->fine);
+        cudaFree(nn->fine_fl);
+        nn->fine = nullptr;
+        nn->fine_fl = nullptr;
+        nn->fine_cells = 0;
+        NCK(nn, lbm::dev_alloc(&nn->fine, 2 * (size_t)nn->nb * cells * 3 * sizeof(float)),
+            "cudaMalloc(fine fields)");
+        NCK(nn, lbm::dev_alloc(&nn->fine_fl, (size_t)nn->nb * cells), "cudaMalloc(fine fluid)");
+        nn->fine_cells = cells;
+    }
+    const long long Pc = (long long)n * nn->H * nn->W, P = (long long)n * cells;
+    float* f0 = nn->fine;
+    float* f1 = nn->fine + (size_t)nn->nb * cells * 3;
+    // the coarse fields go through the output stage's buffer, free between calls
+    NCK(nn, cudaMemcpyAsync(nn->tmp3, y, Pc * 3 * sizeof(float), cudaMemcpyHostToDevice, s),
+        "cudaMemcpyAsync(H2D)");
+    NCK(nn, cudaMemcpyAsync(nn->fine_fl, fluid, P, cudaMemcpyHostToDevice, s),
+        "cudaMemcpyAsync(H2D)");
+    const FluidBytes fl{nn->fine_fl};
+    prolong_kernel<<<grid_of(P), kThreads, 0, s>>>(nn->tmp3, nn->fine_fl, f0, n, nn->H, nn->W,
+                                                   factor);
+    NCK(nn, cudaGetLastError(), "prolongation");
+    out_smooth_kernel<false, false><<<grid_of(P), kThreads, 0, s>>>(f0, 3, fl, f1, 3, n, H, W);
+    NCK(nn, cudaGetLastError(), "output smoothing (fine)");
+    stagger_sum_kernel<<<n, kThreads, 0, s>>>(f1, fl, nn->ssum, H, W);
+    NCK(nn, cudaGetLastError(), "staggered sums (fine)");
+    stagger_apply_kernel<<<grid_of(P), kThreads, 0, s>>>(f1, fl, nn->ssum, f0, P, H, W);
+    NCK(nn, cudaGetLastError(), "staggered projection (fine)");
+    nn->launches += 4;
+    NCK(nn, cudaMemcpyAsync(out, f0, P * 3 * sizeof(float), cudaMemcpyDeviceToHost, s),
+        "cudaMemcpyAsync(D2H)");
+    NCK(nn, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return LBM_OK;
 }
 
 lbm_status lbm_nn_gradients(lbm_nn* nn, const float* x, const float* target,

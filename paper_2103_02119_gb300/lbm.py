@@ -141,6 +141,8 @@ def _load():
     L.lbm_nn_get_params.argtypes = [_P, _F]
     L.lbm_nn_set_params.argtypes = [_P, _F]
     L.lbm_nn_forward.argtypes = [_P, _F, ctypes.c_int, _F]
+    L.lbm_nn_prolong.argtypes = [_P, _F, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_uint8), _F]
     L.lbm_nn_gradients.argtypes = [_P, _F, _F, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int,
                                    _F, _F]
     L.lbm_nn_train_step.argtypes = [_P, _F, _F, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int,
@@ -567,6 +569,20 @@ def lbm_nn_forward(nn, x):
     y = np.empty(x.shape[:3] + (3,), np.float32)
     _ncheck(lib.lbm_nn_forward(nn, _fptr(x), x.shape[0], _fptr(y)), nn)
     return y
+
+
+def lbm_nn_prolong(nn, y, factor, fluid):
+    """y (n, h, w, 3) network outputs, fluid (n, h f, w f) fine fluid flags ->
+    (n, h f, w f, 3) prolonged fields after the output stage."""
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    f = np.ascontiguousarray(fluid, dtype=np.uint8)
+    n, h, w = y.shape[:3]
+    if factor >= 1 and f.shape != (n, h * factor, w * factor):
+        raise ValueError(f"fluid must have shape {(n, h * factor, w * factor)}")
+    out = np.empty((n, h * max(factor, 0), w * max(factor, 0), 3), np.float32)
+    _ncheck(lib.lbm_nn_prolong(nn, _fptr(y), n, int(factor),
+                               f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _fptr(out)), nn)
+    return out
 
 
 def lbm_nn_gradients(nn, x, target, fluid):

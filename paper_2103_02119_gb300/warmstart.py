@@ -24,7 +24,7 @@ import numpy as np
 
 from . import workloads as W
 from .lbm import (Batch, lbm_nn_create, lbm_nn_destroy, lbm_nn_forward, lbm_nn_get_params,
-                  lbm_nn_set_params, lbm_nn_train_step)
+                  lbm_nn_prolong, lbm_nn_set_params, lbm_nn_train_step)
 
 
 def cavity_set(count, seed, n=64, a_range=(0.5, 1.0), re_range=(20.0, 200.0),
@@ -75,6 +75,26 @@ def fields_of(wl, y):
     U = wl.info["U"]
     rho = 1.0 + y[..., 0].astype(np.float64) * U * U / wl.cs2
     return rho, y[..., 1].astype(np.float64) * U, y[..., 2].astype(np.float64) * U
+
+
+def coarsen(x, t, fluid, factor):
+    """Inputs, targets and fluid flags of a network working on a grid
+    `factor` times coarser than the instances (data preparation; the network
+    sees the whole cavity within its receptive field): inputs averaged over
+    factor x factor blocks (channel 0 becomes the block's solid fraction, so a
+    coarse cell is fluid where less than half of its block is solid), targets
+    averaged over the block's fluid cells."""
+    if factor == 1:
+        return x, t, fluid
+    n, H, W, _ = x.shape
+    h, w = H // factor, W // factor
+    blk = lambda a: a.reshape(n, h, factor, w, factor, *a.shape[3:])
+    xc = blk(x).mean(axis=(2, 4)).astype(np.float32)
+    fl = blk(fluid.astype(np.float64))
+    cnt = fl.sum(axis=(2, 4))
+    tc = (blk(t) * fl[..., None]).sum(axis=(2, 4)) / np.maximum(cnt, 1.0)[..., None]
+    flc = (xc[..., 0] < 0.5).astype(np.uint8)
+    return xc, (tc * flc[..., None]).astype(np.float32), flc
 
 
 def fluid_of(wls):
@@ -139,6 +159,21 @@ class WarmStart:
         out = []
         for i in range(0, len(x), self.max_batch):
             out.append(lbm_nn_forward(self.nn, x[i:i + self.max_batch]))
+        return np.concatenate(out)
+
+    def predict_fine(self, x, fluid, factor):
+        """Predictions for instances `factor` times finer than the network's
+        grid: the network on the block-averaged inputs, then its outputs
+        prolonged to the instances' grid and put through the output stage
+        there (lbm_nn_prolong, on the GPU).  x: the instances' input planes;
+        fluid: their fluid flags."""
+        if factor == 1:
+            return self.predict(x)
+        xc, _, _ = coarsen(x, x[..., :3], fluid, factor)
+        out = []
+        for i in range(0, len(x), self.max_batch):
+            y = lbm_nn_forward(self.nn, xc[i:i + self.max_batch])
+            out.append(lbm_nn_prolong(self.nn, y, factor, fluid[i:i + self.max_batch]))
         return np.concatenate(out)
 
     def train(self, x, t, fluid, epochs, lr=1e-3, seed=0, lr_final=None):

@@ -207,3 +207,29 @@ def test_warm_start_against_rest_start(orc):
         print("instance", k, "oracle steps", steps, "max |du| / U GPU vs oracle", d)
         assert d <= 1e-4, (k, d)
     ws.close()
+
+
+def test_prolong_matches_reference():
+    """lbm_nn_prolong (bilinear prolongation, then the output stage on the
+    fine grid with the fine fluid flags) against the FP64 reference, element
+    by element: FP32 interpolation and smoothing round at ~1e-7 of the
+    values, the staggered sums are FP64 on both sides.  Three factors in a
+    row (the fine buffers grow between the calls), a batch below max_batch,
+    ragged solid patterns."""
+    from paper_2103_02119_gb300 import lbm as L
+    nn = L.lbm_nn_create([8, 16], 3, 8, 12)
+    rng = np.random.default_rng(31)
+    for factor, n in ((1, 3), (3, 2), (4, 3)):
+        y = rng.normal(size=(n, 8, 12, 3)).astype(np.float32)
+        fl = rng.random((n, 8 * factor, 12 * factor)) > 0.12
+        got = L.lbm_nn_prolong(nn, y, factor, fl)
+        ref = S.prolong_stage(y.astype(np.float64), factor, fl)
+        scale = float(np.abs(ref).max())
+        assert float(np.abs(got - ref).max()) <= 1e-6 * (1.0 + scale), factor
+        assert np.all(got[~fl] == 0.0)
+    for bad in (0, 17):
+        with pytest.raises(L.LbmError):
+            L.lbm_nn_prolong(nn, y, bad, np.ones((n, 8 * max(bad, 1), 12 * max(bad, 1)), bool))
+    with pytest.raises(L.LbmError):
+        L.lbm_nn_prolong(nn, np.zeros((4, 8, 12, 3), np.float32), 2, np.ones((4, 16, 24), bool))
+    L.lbm_nn_destroy(nn)

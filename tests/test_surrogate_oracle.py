@@ -174,3 +174,64 @@ def test_output_stage_in_the_network_forward():
     for k in range(2):
         assert abs(((-1.0) ** xx * fluid[k] * y[k, :, :, 1]).sum()) < 1e-12
         assert abs(((-1.0) ** yy * fluid[k] * y[k, :, :, 2]).sum()) < 1e-12
+
+
+# ---- prolongation of coarse predictions to a finer lattice ----
+
+def test_prolong_identity_at_factor_one():
+    rng = np.random.default_rng(21)
+    y = rng.normal(size=(2, 5, 7, 3))
+    fl = rng.random((2, 5, 7)) > 0.2
+    assert np.array_equal(S.prolong(y, 1, fl), y * fl[..., None])
+
+
+@pytest.mark.parametrize("factor", [2, 3, 4])
+def test_prolong_reproduces_linear_fields_and_clamps(factor):
+    """Bilinear interpolation between cell centres reproduces a field linear
+    in the coarse centre coordinates; beyond the outermost centres it holds
+    the value at the nearest one (coordinates clamped)."""
+    h, w = 6, 9
+    jj, ii = np.mgrid[0:h, 0:w]
+    lin = lambda xc, yc: 0.3 + 1.7 * xc - 0.9 * yc
+    y = np.stack([lin(ii, jj), 2 * lin(ii, jj), -lin(ii, jj)], axis=-1)[None]
+    H, W = h * factor, w * factor
+    out = S.prolong(y, factor, np.ones((1, H, W), bool))
+    Y, X = np.mgrid[0:H, 0:W]
+    xc = np.clip((X + 0.5) / factor - 0.5, 0, w - 1)
+    yc = np.clip((Y + 0.5) / factor - 0.5, 0, h - 1)
+    ref = lin(xc, yc)
+    assert np.allclose(out[0, ..., 0], ref, atol=1e-12)
+    assert np.allclose(out[0, ..., 1], 2 * ref, atol=1e-12)
+    # the first fine rows lie before the first coarse centre
+    edge = (Y + 0.5) / factor - 0.5 < 0
+    assert np.allclose(out[0][edge][:, 0], lin(xc[edge], 0.0), atol=1e-12)
+
+
+@pytest.mark.parametrize("factor", [2, 4])
+def test_prolong_hat_sums_to_the_cell_count(factor):
+    """A single interior coarse value of 1 spreads into the tensor-product
+    hat of width 2 coarse cells: its fine samples are symmetric about the
+    coarse centre and sum to factor^2 (the coarse cell's share of the
+    partition of unity); a shifted or transposed index breaks both."""
+    h, w = 7, 8
+    y = np.zeros((1, h, w, 3))
+    y[0, 3, 4, 0] = 1.0
+    out = S.prolong(y, factor, np.ones((1, h * factor, w * factor), bool))[0, ..., 0]
+    assert abs(out.sum() - factor ** 2) <= 1e-12
+    rows = slice(3 * factor - factor + 1, 3 * factor + 2 * factor - 1)
+    cols = slice(4 * factor - factor + 1, 4 * factor + 2 * factor - 1)
+    block = out[rows, cols]
+    assert abs(block.sum() - factor ** 2) <= 1e-12
+    assert np.allclose(block, block[::-1, :]) and np.allclose(block, block[:, ::-1])
+
+
+def test_prolong_stage_leaves_no_staggered_momentum():
+    rng = np.random.default_rng(22)
+    y = rng.normal(size=(2, 4, 5, 3))
+    fl = rng.random((2, 12, 15)) > 0.15
+    out = S.prolong_stage(y, 3, fl)
+    Y, X = np.mgrid[0:12, 0:15]
+    for k in range(2):
+        assert abs((out[k, ..., 1] * (-1.0) ** X * fl[k]).sum()) <= 1e-12
+        assert abs((out[k, ..., 2] * (-1.0) ** Y * fl[k]).sum()) <= 1e-12
+        assert np.all(out[k][~fl[k]] == 0.0)
