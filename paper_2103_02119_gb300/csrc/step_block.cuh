@@ -19,8 +19,8 @@
 // Staging.  The populations a row pulls (plane i of the source row
 // y - e_iy, columns x0-4 .. x0+W+3) are brought into shared memory by TMA
 // bulk copies (cp.async.bulk, completion counted on an mbarrier), issued by
-// one lane kStages rows ahead into a ring of kStages stages (four in FP32,
-// three in FP64).  A thread reads its
+// one lane kStages rows ahead into a ring of kStages stages (four in FP32
+// blocks of 128 or more threads, three otherwise).  A thread reads its
 // cells' nine populations with vector shared loads (plus one scalar load for
 // the planes shifted along x) and keeps them in registers until the row
 // collides one iteration later, so a stage is free as soon as its row is
@@ -57,11 +57,16 @@ namespace lbm {
 
 namespace {
 
-// Stage ring depth: copies run kStages rows ahead.  FP32 takes four stages
-// (76.3k against 75.1k MLUPS with three); FP64 three, since a fourth FP64
-// stage leaves room for one block fewer per SM.
-template <typename T>
-__host__ __device__ constexpr int step_stages() { return sizeof(T) == 4 ? 4 : 3; }
+// Stage ring depth: copies run kStages rows ahead.  FP32 blocks of 128 or
+// more threads take four stages (76.3k against 75.1k MLUPS with three on the
+// 2048 x 8192 cavity); narrower FP32 blocks and FP64 take three, where a
+// fourth stage leaves room for one block fewer per SM (64-thread batch
+// blocks: 9 instead of 10 per SM; the 512-lattice sweep 43.1k against 39.3k
+// MLUPS with three).
+template <typename T, int BXT>
+__host__ __device__ constexpr int step_stages() {
+    return sizeof(T) == 4 && BXT >= 128 ? 4 : 3;
+}
 constexpr int kHalo = 4;                // staged columns on each side of a segment
 // Polls of a bounded wait: the drain of the copies in flight always uses
 // kSpinLimit; the wait for a row's data uses the lattice's spin_limit (the
@@ -151,7 +156,7 @@ __host__ __device__ constexpr int step_cells_per_thread() { return 2; }
 // mbarriers, the population stages, the density ring and the link-mask stages
 template <typename T, int BXT>
 constexpr size_t step_smem_bytes() {
-    constexpr int kStages = step_stages<T>();
+    constexpr int kStages = step_stages<T, BXT>();
     constexpr int W = BXT * step_cells_per_thread<T>();
     return 128 + (size_t)kStages * 9 * (W + 2 * kHalo) * sizeof(T) + 4 * (W + 8) * sizeof(T) +
            (size_t)kStages * W;
@@ -172,7 +177,7 @@ __device__ __forceinline__ bool step_block(const T* __restrict__ fin, T* __restr
                                            const PT p, int nbands, int seg, int band,
                                            unsigned char* smem) {
     constexpr int VC = step_cells_per_thread<T>();
-    constexpr int kStages = step_stages<T>();
+    constexpr int kStages = step_stages<T, BXT>();
     constexpr int W = BXT * VC;          // segment width
     constexpr int SW = W + 2 * kHalo;    // staged row width
     constexpr int RW = W + 8;            // density ring row width
