@@ -75,7 +75,7 @@ def parse():
                     help="held-out warm-start instances")
     ap.add_argument("--warm-only", action="store_true",
                     help="print only the warm-start measurement")
-    ap.add_argument("--warm-epochs", type=int, default=40)
+    ap.add_argument("--warm-epochs", type=int, default=80)
     ap.add_argument("--warm-coarse", type=int, default=1,
                     help="network grid this many times coarser than the instances "
                          "(predictions prolonged on the GPU)")
