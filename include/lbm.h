@@ -301,7 +301,7 @@ const char* lbm_last_error(const lbm_handle* h);
  * Every step of a batch is one launch of a persistent kernel per group of
  * lattices, each walking a list of (lattice, column segment, band of rows)
  * work items of its group's active lattices.  When they fit, the active
- * lattices form up to 4 groups of one scheme and at most ~170 lattices
+ * lattices form up to 4 groups of one scheme and at most 180 lattices
  * each, whose parameter tables sit in constant memory (one table per group,
  * shared by every batch of the device: a batch whose tables another batch
  * has replaced re-uploads them after a device synchronisation; batches

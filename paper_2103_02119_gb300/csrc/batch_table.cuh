@@ -101,15 +101,12 @@ int table_occ_bx() {
 
 }  // namespace
 
-cudaError_t LBM_SLOT_NAME(batch_table_upload_)(const BatchTableLattice* lat, int n, int total,
-                                               cudaStream_t s) {
+cudaError_t LBM_SLOT_NAME(batch_table_upload_)(const BatchTableLattice* lat, const int* begin,
+                                               int n, cudaStream_t s) {
     if (n < 1 || n > kBatchTableCap) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemcpyToSymbolAsync(c_table, lat, sizeof(BatchTableLattice) * (size_t)n, 0,
                                             cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    int begin[kBatchTableCap + 1];
-    for (int k = 0; k < n; ++k) begin[k] = lat[k].begin;
-    begin[n] = total;
     e = cudaMemcpyToSymbolAsync(c_table_begin, begin, sizeof(int) * (size_t)(n + 1), 0,
                                 cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;

@@ -1082,7 +1082,7 @@ struct lbm_batch {
     int graw[lbm::kBatchTables] = {};
     int ggrid[lbm::kBatchTables] = {};
     std::vector<lbm::BatchTableLattice> gtab[lbm::kBatchTables];
-    int gtotal[lbm::kBatchTables] = {};
+    std::vector<int> gbegin[lbm::kBatchTables];  // first work item of each, then the total
     unsigned long long serial = 0;   // which batch the device's tables hold
     int device = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -1251,26 +1251,42 @@ void plan_groups(lbm_batch* b) {
                 std::vector<int>& v = ids[w];
                 std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return work(x) > work(y); });
                 std::vector<long long> load(ng, 0);
-                for (int j = 0; j < ng; ++j) b->gtab[g0 + j].clear();
+                std::vector<std::vector<int>> members(ng);
                 for (int k : v) {
                     int best = -1;
                     for (int j = 0; j < ng; ++j)
-                        if ((int)b->gtab[g0 + j].size() < cap && (best < 0 || load[j] < load[best]))
+                        if ((int)members[j].size() < cap && (best < 0 || load[j] < load[best]))
                             best = j;
-                    lbm::BatchTableLattice e;
-                    e.kp = kparams_table(b->lat[k].kp);
-                    e.f[0] = b->lat[k].f[0];
-                    e.f[1] = b->lat[k].f[1];
-                    e.nseg = b->lat[k].nseg;
-                    e.nbands = b->lat[k].nbands;
-                    e.begin = (int)load[best];
+                    members[best].push_back(k);
                     load[best] += work(k);
-                    b->gtab[g0 + best].push_back(e);
                 }
                 for (int j = 0; j < ng; ++j) {
-                    b->graw[g0 + j] = w;
-                    b->gtotal[g0 + j] = (int)load[j];
-                    b->ggrid[g0 + j] = lbm::batch_table_occupancy(g0 + j, b->bx) * b->sms;
+                    // the tallest bands first: the last work items a group's
+                    // blocks take are then its shortest, which shortens the
+                    // kernel's tail
+                    std::vector<int>& m = members[j];
+                    std::stable_sort(m.begin(), m.end(), [&](int x, int y) {
+                        return (long long)b->p[x].ny * b->lat[y].nbands >
+                               (long long)b->p[y].ny * b->lat[x].nbands;
+                    });
+                    const int g = g0 + j;
+                    b->gtab[g].clear();
+                    b->gbegin[g].clear();
+                    int at = 0;
+                    for (int k : m) {
+                        lbm::BatchTableLattice e;
+                        e.kp = kparams_table(b->lat[k].kp);
+                        e.f[0] = b->lat[k].f[0];
+                        e.f[1] = b->lat[k].f[1];
+                        e.nseg = b->lat[k].nseg;
+                        e.nbands = b->lat[k].nbands;
+                        b->gtab[g].push_back(e);
+                        b->gbegin[g].push_back(at);
+                        at += (int)work(k);
+                    }
+                    b->gbegin[g].push_back(at);
+                    b->graw[g] = w;
+                    b->ggrid[g] = lbm::batch_table_occupancy(g, b->bx) * b->sms;
                 }
                 g0 += ng;
             }
@@ -1298,8 +1314,8 @@ lbm_status ensure_tables(lbm_batch* b) {
     if (g_table_owner[d] != 0 && g_table_owner[d] != b->serial)
         BCK(b, cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     for (int g = 0; g < b->ngroups; ++g)
-        BCK(b, lbm::batch_table_upload(g, b->gtab[g].data(), (int)b->gtab[g].size(), b->gtotal[g],
-                                       b->stream),
+        BCK(b, lbm::batch_table_upload(g, b->gtab[g].data(), b->gbegin[g].data(),
+                                       (int)b->gtab[g].size(), b->stream),
             "upload of a batch lattice table");
     g_table_owner[d] = b->serial;
     g_table_fresh[d] = true;

@@ -73,20 +73,19 @@ int batch_occupancy(int bx);
 
 // One lattice of a group of a batch, in a constant-memory table
 // (batch_table.cuh): its parameters with the collision constants stored once
-// each, its buffers and its work items (nseg * nbands, in the group's list
-// from `begin` on, which the table keeps in an array of its own).
+// each, its buffers and its work items (nseg * nbands; where they start in
+// the group's list the table keeps in an array of its own).
 struct BatchTableLattice {
     KParams<float, CollConstF> kp;
     float* f[2];
     int nseg, nbands;
-    int begin;  // host side only
 };
 // Tables (translation units rc_batch_t0.cu ..), and lattices per table: a
 // module's constant bank holds 64 KiB.
 constexpr int kBatchTables = 4;
-constexpr int kBatchTableCap = 60000 / (int)sizeof(BatchTableLattice);
+constexpr int kBatchTableCap = 62000 / (int)sizeof(BatchTableLattice);
 #define LBM_DECLARE_BATCH_TABLE(S)                                                         \
-    cudaError_t batch_table_upload_##S(const BatchTableLattice* lat, int n, int total,      \
+    cudaError_t batch_table_upload_##S(const BatchTableLattice* lat, const int* begin, int n, \
                                        cudaStream_t s);                                     \
     cudaError_t batch_table_launch_##S(int parity, int bx, int grid, int raw, cudaStream_t s); \
     int batch_table_occupancy_##S(int bx);
@@ -95,15 +94,16 @@ LBM_DECLARE_BATCH_TABLE(1)
 LBM_DECLARE_BATCH_TABLE(2)
 LBM_DECLARE_BATCH_TABLE(3)
 #undef LBM_DECLARE_BATCH_TABLE
-// Table `slot`: copy n lattices (host array) with `total` work items into it,
+// Table `slot`: copy n lattices (host array) and their first work items
+// begin[0 .. n] (begin[n]: the group's number of work items) into it,
 // asynchronously on s (after the kernels of the slot that were issued before
 // on s; the caller orders them).
-inline cudaError_t batch_table_upload(int slot, const BatchTableLattice* lat, int n, int total,
-                                      cudaStream_t s) {
-    return slot == 0   ? batch_table_upload_0(lat, n, total, s)
-           : slot == 1 ? batch_table_upload_1(lat, n, total, s)
-           : slot == 2 ? batch_table_upload_2(lat, n, total, s)
-                       : batch_table_upload_3(lat, n, total, s);
+inline cudaError_t batch_table_upload(int slot, const BatchTableLattice* lat, const int* begin,
+                                      int n, cudaStream_t s) {
+    return slot == 0   ? batch_table_upload_0(lat, begin, n, s)
+           : slot == 1 ? batch_table_upload_1(lat, begin, n, s)
+           : slot == 2 ? batch_table_upload_2(lat, begin, n, s)
+                       : batch_table_upload_3(lat, begin, n, s);
 }
 // One step of every lattice of table `slot` (all of one scheme: raw = 1 for
 // RNR-LBM), from buffer f[parity], on a persistent grid of `grid` blocks.

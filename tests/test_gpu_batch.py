@@ -160,7 +160,7 @@ def _many(count, seed):
 @pytest.mark.parametrize("count,groups", [(400, 3), (900, 0)])
 def test_table_groups_and_fallback(count, groups):
     """400 lattices (266 RC-LBM, 134 RNR-LBM) fill three constant-memory
-    tables (at most 170 lattices each, one scheme each); 900 would need six
+    tables (at most 180 lattices each, one scheme each); 900 would need six
     of the four and step from the global table.  Either way a sample of lattices equals single-lattice
     handles bit for bit, across graph replays and a retirement that changes
     the groups."""
