@@ -86,15 +86,26 @@ def coarsen(x, t, fluid, factor):
     averaged over the block's fluid cells."""
     if factor == 1:
         return x, t, fluid
+    xc = coarsen_inputs(x, factor)
     n, H, W, _ = x.shape
     h, w = H // factor, W // factor
     blk = lambda a: a.reshape(n, h, factor, w, factor, *a.shape[3:])
-    xc = blk(x).mean(axis=(2, 4)).astype(np.float32)
     fl = blk(fluid.astype(np.float64))
     cnt = fl.sum(axis=(2, 4))
     tc = (blk(t) * fl[..., None]).sum(axis=(2, 4)) / np.maximum(cnt, 1.0)[..., None]
     flc = (xc[..., 0] < 0.5).astype(np.uint8)
     return xc, (tc * flc[..., None]).astype(np.float32), flc
+
+
+def coarsen_inputs(x, factor):
+    """Input planes averaged over factor x factor blocks (see coarsen)."""
+    n, H, W, c = x.shape
+    if factor < 1 or H % factor or W % factor:
+        raise ValueError(f"{H} x {W} instances do not split into {factor} x {factor} blocks")
+    if factor == 1:
+        return x
+    return x.reshape(n, H // factor, factor, W // factor, factor, c).mean(axis=(2, 4)).astype(
+        np.float32)
 
 
 def fluid_of(wls):
@@ -169,7 +180,7 @@ class WarmStart:
         fluid: their fluid flags."""
         if factor == 1:
             return self.predict(x)
-        xc, _, _ = coarsen(x, x[..., :3], fluid, factor)
+        xc = coarsen_inputs(x, factor)
         out = []
         for i in range(0, len(x), self.max_batch):
             y = lbm_nn_forward(self.nn, xc[i:i + self.max_batch])
