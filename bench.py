@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--mask", action="store_true",
+                    help="the main workload with the solid mask of the with_mask line")
     ap.add_argument("--no-mask", action="store_true",
                     help="skip the same cavity with a solid mask")
     ap.add_argument("--no-peaks", action="store_true",
@@ -93,15 +95,23 @@ def parse():
     return ap.parse_args()
 
 
+def with_obstacles(wl):
+    """The cavity with seeded solid rectangles (the masked workload)."""
+    from paper_2103_02119_gb300 import workloads as W
+    return wl.with_(mask=W.random_obstacles(wl.nx, wl.ny, seed=3, coverage=0.016))
+
+
 def workload(args):
     from paper_2103_02119_gb300 import workloads as W
-    return W.cavity(args.nx, args.ny, 0.25, 0.04, 0.05, 1000.0)
+    wl = W.cavity(args.nx, args.ny, 0.25, 0.04, 0.05, 1000.0)
+    return with_obstacles(wl) if getattr(args, "mask", False) else wl
 
 
 def workload_config(args, wl):
     return {
         "workload": f"lid-driven cavity {wl.nx}x{wl.ny} cells, a=0.25, Re=1000, "
-                    f"lid u=0.05, FP{args.precision} storage",
+                    f"lid u=0.05, FP{args.precision} storage"
+                    + (", seeded solid rectangles (link mask)" if wl.mask is not None else ""),
         "nx": wl.nx, "ny": wl.ny, "cells": wl.cells, "a": wl.a, "cs2": wl.cs2,
         "lid_u": 0.05, "Re": 1000, "nu": wl.info["nu"],
         "layout": "SoA 9 planes, two buffers, pull streaming",
@@ -207,25 +217,26 @@ def step_kernel_hash(csrc=None):
     return h.hexdigest()[:16]
 
 
-def profiled(precision, key):
-    """A per-cell figure of the committed ncu summary of the step kernel, or
-    None when the kernel has changed since it was captured."""
+def profiled(precision, key, mask=False):
+    """A per-cell figure of the committed ncu summary of the step kernel
+    (with a solid mask: its own entry), or None when the kernel has changed
+    since it was captured."""
     path = os.path.join(ROOT, "profiles", "rc_step_traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    e = d.get(f"fp{precision}")
+    e = d.get(f"fp{precision}" + ("_mask" if mask else ""))
     if not e or e.get("kernel_sha") != step_kernel_hash():
         return None
     return e.get(key)
 
 
-def profiled_traffic(precision, cells):
+def profiled_traffic(precision, cells, mask=False):
     """DRAM bytes per launch from the committed ncu summary, scaled to this
     grid, or None when the kernel has changed since it was captured."""
-    b = profiled(precision, "dram_bytes_per_cell")
+    b = profiled(precision, "dram_bytes_per_cell", mask)
     return None if b is None else b * cells
 
 
@@ -696,13 +707,17 @@ def main():
     cells = wl.cells
     value = world * cells * args.steps / secs / 1e6
     per_launch = secs / args.steps
-    algo_bytes = BYTES_PER_CELL[args.precision] * cells
+    # a solid mask adds its link-mask byte to the algorithmic bytes
+    bpc_main = BYTES_PER_CELL[args.precision] + (1 if args.mask else 0)
+    algo_bytes = bpc_main * cells
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / per_launch / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(args.precision, cells),
-                "peak_kind": peak_kind, "kernel": f"rc_step_kernel<fp{args.precision}>",
-                "algorithmic_bytes_per_cell": BYTES_PER_CELL[args.precision]}
+                "frac": achieved / peak,
+                "traffic": profiled_traffic(args.precision, cells, args.mask),
+                "peak_kind": peak_kind,
+                "kernel": f"rc_step_kernel<fp{args.precision}{', mask' if args.mask else ''}>",
+                "algorithmic_bytes_per_cell": bpc_main}
     e2e_res = None if args.no_e2e else e2e(lat, wl, torch, args.e2e_chunk, args.e2e_steps)
     peaks = None
     if rank == 0 and not args.no_peaks:
@@ -744,7 +759,7 @@ def main():
     with_mask = None
     if rank == 0 and not args.no_mask:
         from paper_2103_02119_gb300 import workloads as W
-        wm = wl.with_(mask=W.random_obstacles(wl.nx, wl.ny, seed=3, coverage=0.016))
+        wm = with_obstacles(wl) if wl.mask is None else wl
         latm = Lattice.from_workload(wm, precision=args.precision, stream=stream)
         nm = max(100, args.steps // 10)
         sm, _ = time_steps(latm, torch, nm, 10, barrier)
@@ -754,7 +769,8 @@ def main():
         with_mask = {"value": cells * nm / sm / 1e6, "unit": "MLUPS", "steps": nm,
                      "solid_fraction": float(wm.mask.mean()),
                      "roofline": {"bound": "hbm", "achieved": am, "peak": peak, "unit": "GB/s",
-                                  "frac": am / peak, "algorithmic_bytes_per_cell": bpc}}
+                                  "frac": am / peak, "algorithmic_bytes_per_cell": bpc,
+                                  "traffic": profiled_traffic(args.precision, cells, True)}}
 
     batch = None
     if rank == 0 and not args.no_batch:
