@@ -543,6 +543,36 @@ def small_lattice(torch):
     return out
 
 
+# -------------------------------------------------------- config 2 lattices --
+
+def config2_throughput(torch, steps=200):
+    """Config 2's lattices (2048 x 1024, fully periodic, Taylor-Green vortex,
+    u0 = 0.02, nu = 1e-2, c_s^2 = 1/3 at a = 1 and 0.3 a^2 below): the step
+    in FP32 and FP64 at each aspect ratio, from the seeded initial field."""
+    from paper_2103_02119_gb300 import workloads as W
+    from paper_2103_02119_gb300.lbm import Lattice
+    stream = torch.cuda.current_stream()
+    out = {"workload": "Taylor-Green vortex 2048x1024, fully periodic, u0=0.02, nu=1e-2",
+           "steps": steps}
+    for a in (0.25, 0.5, 1.0):
+        cs2 = 1 / 3 if a == 1.0 else 0.3 * a * a
+        wl = W.taylor_green(2048, 1024, a, cs2, 1e-2, u0=0.02, seed=0, wavelength=256)
+        for prec in (32, 64):
+            lat = Lattice.from_workload(wl, precision=prec, stream=stream)
+            n = steps if prec == 32 else max(20, steps // 10)
+            lat.step(5)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(n)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[f"a{a}_fp{prec}_mlups"] = wl.cells * n / (e0.elapsed_time(e1) / 1e3) / 1e6
+            lat.close()
+    return out
+
+
 # ---------------------------------------------------------------- warm start --
 
 def warm_start_measure(torch, ntrain, epochs, n=32, ntest=32, coarse=1):
@@ -779,6 +809,7 @@ def main():
                                                            args.ttr_max_steps)
 
     small = small_lattice(torch) if rank == 0 and not args.no_batch else None
+    config2 = config2_throughput(torch) if rank == 0 and not args.no_fp64 else None
 
     warm = None
     if rank == 0 and not args.no_warm:
@@ -803,6 +834,7 @@ def main():
             "config": workload_config(args, wl), "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e_res, "gpu_launches": launches,
             "clocks": clk.summary(), "fp64": fp64, "batch": batch, "small_lattice": small,
+            "config2": config2,
             "warm_start": warm, "repo_peaks": peaks, "with_mask": with_mask,
         }
         print(json.dumps(line), flush=True)
