@@ -92,3 +92,22 @@ def test_kernel_hash_ignores_comments_not_code(tmp_path):
     assert bench.step_kernel_hash(str(tmp_path)) == base
     p.write_text(text.replace("constexpr int kHalo = 4;", "constexpr int kHalo = 8;", 1))
     assert bench.step_kernel_hash(str(tmp_path)) != base
+
+
+def test_recorded_traffic_per_variant():
+    """The committed ncu traffic record holds the FP32 step with and without
+    a link mask and the FP64 step, each tied to the current kernels' code;
+    bench.py scales the per-cell bytes to its grid and reads the masked
+    entry only for a masked line."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    with open(os.path.join(ROOT, "profiles", "rc_step_traffic.json")) as fh:
+        rec = json.load(fh)
+    cells = 2048 * 8192
+    for key, prec, mask, algo in (("fp32", 32, False, 72), ("fp32_mask", 32, True, 73),
+                                  ("fp64", 64, False, 144)):
+        e = rec[key]
+        assert e["kernel_sha"] == bench.step_kernel_hash(), key
+        assert abs(e["dram_bytes_per_cell"] - algo) <= 0.03 * algo, key
+        assert bench.profiled_traffic(prec, cells, mask) == e["dram_bytes_per_cell"] * cells
