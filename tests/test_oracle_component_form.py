@@ -18,7 +18,8 @@ The component form (Sec. 4, the RC-LBE and its algorithm):
   central moments M0, M1, M2 about u, the raw moments are R0 = M0,
   R1 = M1 + u M0, R2 = M2 + 2 u M1 + u^2 M0, and the node values are
   R0 - R2 / c^2 at 0 and (R2 / c^2 +- R1 / c) / 2 at +-c.
-None of this uses the oracle's matrices.
+The raw-moment scheme (Sec. 3) gets the same treatment below.  None of this
+uses the oracle's matrices.
 """
 import numpy as np
 import pytest
@@ -124,5 +125,82 @@ def test_matrix_form_equals_component_form(orc, a, cs2, iso, gi):
                                   use_gi_corr=gi)
         got, (sx, sy) = orc.collide_cell(p, f, dxr, dyr)
         ref, (rx, ry) = collide_component_form(f, a, cs2, w, Fx, Fy, dxr, dyr, iso, gi)
+        assert np.abs(got - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max()), (got - ref)
+        assert abs(sx - rx) <= 1e-12 * max(1.0, abs(rx)) and abs(sy - ry) <= 1e-12 * max(1.0, abs(ry))
+
+
+def collide_raw_component_form(f, a, cs2, w, Fx, Fy, dxr, dyr, iso=1, gi=1):
+    """The raw-moment scheme (RNR-LBM, Sec. 3) written out: raw moments
+    m_j = sum f_i P_j(e_i) of the Eq. 3 basis, the equilibria of Eq. 12 (m8
+    read as rho cs2^2 + rho cs2 |u|^2 + rho ux^2 uy^2), the corrections of
+    Eq. 23-26 with the strain rates of Eq. 37-38, and the source moments
+    Phi_j = F . grad P_j (u) (the raw moments of a source whose central
+    moments are (0, Fx, Fy, 0, ...)); back to populations as in the central
+    form, about u = 0."""
+    ex, ey = EX, EY * a
+    rho = f.sum()
+    ux = ((f * ex).sum() + Fx / 2) / rho
+    uy = ((f * ey).sum() + Fy / 2) / rho
+    P = [lambda x, y: 1.0 + 0 * x, lambda x, y: x, lambda x, y: y,
+         lambda x, y: x * x + y * y, lambda x, y: x * x - y * y, lambda x, y: x * y,
+         lambda x, y: x * x * y, lambda x, y: x * y * y, lambda x, y: x * x * y * y]
+    grad = [(0.0, 0.0), (1.0, 0.0), (0.0, 1.0), (2 * ux, 2 * uy), (2 * ux, -2 * uy), (uy, ux),
+            (2 * ux * uy, ux * ux), (uy * uy, 2 * ux * uy),
+            (2 * ux * uy * uy, 2 * ux * ux * uy)]
+    m = [(f * Pj(ex, ey)).sum() for Pj in P]
+    u2 = ux * ux + uy * uy
+    meq = [rho, rho * ux, rho * uy, 2 * rho * cs2 + rho * u2, rho * (ux * ux - uy * uy),
+           rho * ux * uy, cs2 * rho * uy + rho * ux * ux * uy, cs2 * rho * ux + rho * ux * uy * uy,
+           rho * cs2 * cs2 + rho * cs2 * u2 + rho * ux * ux * uy * uy]
+    N3, N4 = m[3] - meq[3], m[4] - meq[4]
+    B1 = rho * (-2 * cs2 / w[3] - (-3 * cs2 + 1) / 2 + 3 * ux ** 2 / 2)
+    B2 = rho * (-2 * cs2 / w[3] - (-3 * cs2 + a * a) / 2 + 3 * uy ** 2 / 2)
+    C1 = rho * (-2 * cs2 / w[4] - (-3 * cs2 + 1) / 2 + 3 * ux ** 2 / 2)
+    C2 = rho * (2 * cs2 / w[4] - (3 * cs2 - a * a) / 2 - 3 * uy ** 2 / 2)
+    R3 = N3 - (3 * cs2 - 1) / 2 * ux * dxr - (3 * cs2 - a * a) / 2 * uy * dyr
+    R4 = N4 - (3 * cs2 - 1) / 2 * ux * dxr - (-3 * cs2 + a * a) / 2 * uy * dyr
+    dxux = (C2 * R3 - B2 * R4) / (C2 * B1 - C1 * B2)
+    dyuy = (C1 * R3 - B1 * R4) / (C1 * B2 - C2 * B1)
+    t3, t4 = 1 / w[3] - 0.5, 1 / w[4] - 0.5
+    m3s = t3 * ((-3 * cs2 + 1) * rho * dxux + (-3 * cs2 + a * a) * rho * dyuy
+                + (-3 * cs2 + 1) * ux * dxr + (-3 * cs2 + a * a) * uy * dyr)
+    m4s = t4 * ((-3 * cs2 + 1) * rho * dxux + (3 * cs2 - a * a) * rho * dyuy
+                + (-3 * cs2 + 1) * ux * dxr + (3 * cs2 - a * a) * uy * dyr)
+    m3G = -3 * rho * t3 * (ux ** 2 * dxux + uy ** 2 * dyuy)
+    m4G = -3 * rho * t4 * (ux ** 2 * dxux - uy ** 2 * dyuy)
+    meq[3] += iso * m3s + gi * m3G
+    meq[4] += iso * m4s + gi * m4G
+    phi = [gx * Fx + gy * Fy for gx, gy in grad]
+    mt = [m[j] + w[j] * (meq[j] - m[j]) + (1 - w[j] / 2) * phi[j] for j in range(9)]
+    kt = {(0, 0): mt[0], (1, 0): mt[1], (0, 1): mt[2], (2, 0): (mt[3] + mt[4]) / 2,
+          (0, 2): (mt[3] - mt[4]) / 2, (1, 1): mt[5], (2, 1): mt[6], (1, 2): mt[7],
+          (2, 2): mt[8]}
+    h = {}
+    for q in range(3):
+        lo, mid, hi = invert_axis(kt[0, q], kt[1, q], kt[2, q], 0.0, 1.0)
+        h[q] = {-1: lo, 0: mid, 1: hi}
+    out = np.zeros(9)
+    for X in (-1, 0, 1):
+        lo, mid, hi = invert_axis(h[0][X], h[1][X], h[2][X], 0.0, a)
+        for Y, v in ((-1, lo), (0, mid), (1, hi)):
+            out[int(np.flatnonzero((EX == X) & (EY == Y))[0])] = v
+    return out, (dxux, dyuy)
+
+
+@pytest.mark.parametrize("a,cs2", [(1.0, 1 / 3), (0.5, 0.075), (0.25, 0.01875)])
+@pytest.mark.parametrize("iso,gi", [(1, 1), (0, 0)])
+def test_raw_moment_scheme_matrix_form_equals_component_form(orc, a, cs2, iso, gi):
+    rng = np.random.default_rng(int(500 * a) + 7 * iso + gi)
+    for _ in range(25):
+        f = random_cell(rng, a, cs2)
+        w = [1.0, 1.0, 1.0, rng.uniform(0.6, 1.9), rng.uniform(0.6, 1.9),
+             rng.uniform(0.6, 1.9), rng.uniform(0.5, 1.5), rng.uniform(0.5, 1.5),
+             rng.uniform(0.5, 1.5)]
+        Fx, Fy = rng.normal(0, 1e-3, 2)
+        dxr, dyr = rng.normal(0, 1e-2, 2)
+        p = orc.OracleParams.make(8, 8, a, cs2, w, Fx=Fx, Fy=Fy, use_iso_corr=iso,
+                                  use_gi_corr=gi, scheme="rnr")
+        got, (sx, sy) = orc.collide_cell(p, f, dxr, dyr)
+        ref, (rx, ry) = collide_raw_component_form(f, a, cs2, w, Fx, Fy, dxr, dyr, iso, gi)
         assert np.abs(got - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max()), (got - ref)
         assert abs(sx - rx) <= 1e-12 * max(1.0, abs(rx)) and abs(sy - ry) <= 1e-12 * max(1.0, abs(ry))
